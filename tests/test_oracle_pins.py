@@ -1,0 +1,336 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics
+(closed forms, exact diagonalisation, invariants, finite differences) - no GPU.
+
+Each test names what a plausible mistake in the oracle would break."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+
+from oracle import dense_k, free_electron
+from oracle.sq_oracle import (K_PAIRS, NodeRegion, Problem, cheb_coeffs, chebyshev_columns, contract,
+                              entropy_fn, fd_coefficients, fd_weights, fermi, fermi_bisect, lanczos_bounds,
+                              node_moments, primed, run)
+from workloads import make_instance, tiny_instance
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- finite differences
+@pytest.mark.parametrize("n_o", [1, 2, 3, 4, 5, 6])
+def test_fd_weights_match_vandermonde_solve(n_o):
+    """Closed-form central weights == the unique weights exact on polynomials of degree
+    <= 2 n_o (Taylor / Vandermonde conditions solved independently)."""
+    w, g = fd_weights(n_o)
+    p = np.arange(1, n_o + 1, dtype=np.float64)
+    # second derivative: sum_p w_p 2 p^(2k) = 2 delta_{k,1} (k = 1..n_o) with symmetric taps
+    A = np.array([2.0 * p ** (2 * k) for k in range(1, n_o + 1)])
+    rhs = np.zeros(n_o)
+    rhs[0] = 2.0
+    np.testing.assert_allclose(w[1:], np.linalg.solve(A, rhs), rtol=1e-10, atol=1e-13)
+    assert abs(w[0] + 2.0 * w[1:].sum()) < 1e-13
+    # first derivative: sum_p g_p 2 p^(2k-1) = delta_{k,1}
+    A1 = np.array([2.0 * p ** (2 * k - 1) for k in range(1, n_o + 1)])
+    rhs1 = np.zeros(n_o)
+    rhs1[0] = 1.0
+    np.testing.assert_allclose(g[1:], np.linalg.solve(A1, rhs1), rtol=1e-10, atol=1e-13)
+
+
+def test_fd_weights_n_o_3_values():
+    w, g = fd_weights(3)
+    np.testing.assert_allclose(w, [-49.0 / 18.0, 1.5, -0.15, 1.0 / 90.0], rtol=1e-14)
+    np.testing.assert_allclose(g, [0.0, 0.75, -0.15, 1.0 / 60.0], rtol=1e-14)
+
+
+def test_fd_spectral_sup():
+    """sup of the 1-D second-difference symbol -w0 - 2 sum w_p cos(p t): 6.044 (n_o=3), 7.073 (n_o=6)."""
+    t = np.linspace(0, math.pi, 20001)
+    for n_o, want in ((3, 6.044), (6, 7.073)):
+        w, _ = fd_weights(n_o)
+        s = -w[0] - 2.0 * sum(w[p] * np.cos(p * t) for p in range(1, n_o + 1))
+        assert abs(s.max() - want) < 2e-3
+        assert s.min() > -1e-12           # the discrete -Laplacian is positive semidefinite
+
+
+# ---------------------------------------------------------------- coefficients
+def test_cheb_coeffs_match_adaptive_quadrature():
+    """c^j = (2/pi) int g(r) T_j(r)/sqrt(1-r^2) dr (Sec. 4) against adaptive quadrature
+    in theta (r = cos theta) - catches a wrong node set, weight or primed-sum convention."""
+    mu_hat, sig_hat = 0.13, 0.07
+
+    def g(r):
+        return fermi((r - mu_hat) / sig_hat)
+    c = cheb_coeffs(g, 40, 2048)
+    for j in (0, 1, 2, 7, 25, 40):
+        ref, _ = scipy.integrate.quad(lambda th: g(math.cos(th)) * math.cos(j * th), 0.0, math.pi,
+                                      limit=400, epsabs=1e-15, epsrel=1e-13)
+        assert abs(c[j] - 2.0 / math.pi * ref) < 1e-12
+    # the primed series of enough terms reproduces g inside [-1, 1]
+    c = cheb_coeffs(g, 400, 4096)
+    r = np.linspace(-0.99, 0.99, 37)
+    T = np.cos(np.outer(np.arange(401), np.arccos(r)))
+    approx = (primed(400) * c) @ T
+    assert np.abs(approx - g(r)).max() < 1e-12
+
+
+def test_entropy_stable_form_matches_direct():
+    x = np.linspace(-30, 30, 601)
+    g = 1.0 / (1.0 + np.exp(x))
+    direct = g * np.log(g) + (1 - g) * np.log1p(-g)
+    ok = (g > 1e-12) & (g < 1 - 1e-12)
+    np.testing.assert_allclose(entropy_fn(x)[ok], direct[ok], rtol=1e-9, atol=1e-14)
+    assert entropy_fn(np.array([0.0]))[0] == pytest.approx(-math.log(2.0), rel=1e-15)
+
+
+# ---------------------------------------------------------------- P1: exact polynomial identity
+def _tiny_region(seed=3, n_o=2, half=(3, 3, 3)):
+    inst = tiny_instance(seed=seed, n=(5, 5, 5), h=(0.7, 0.7, 0.7), n_atoms=3, n_o=n_o, r_cut=2.1, n_pl=12,
+                         proj=[{"l": 0, "width": 0.6, "gamma": 1.0, "rcut": 3.0},
+                               {"l": 1, "width": 0.6, "gamma": -0.4, "rcut": 3.0}])
+    prob = Problem(inst)
+    return prob, NodeRegion(prob, np.array([1, 2, 3]), half=np.array(half))
+
+
+def test_p1_recurrence_equals_exact_chebyshev_columns():
+    """t^j from the three-term recurrence == U cos(j arccos Lambda_hat) U^T e_q from eigh of the
+    Kronecker-assembled dense H_q (independent operator construction)."""
+    prob, reg = _tiny_region()
+    H = reg.dense_H()
+    lam, U = np.linalg.eigh(H)
+    lo, hi = lam[0] - 0.3, lam[-1] + 0.2
+    chi_q, zeta_q = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    cols = chebyshev_columns(reg, chi_q, zeta_q, 12)
+    e = reg.unit().reshape(-1)
+    th = np.arccos((lam - chi_q) / zeta_q)
+    for j, t in enumerate(cols):
+        exact = U @ (np.cos(j * th) * (U.T @ e))
+        assert np.abs(t.reshape(-1) - exact).max() < 1e-12 * max(1.0, np.abs(exact).max())
+
+
+def test_p1_moments_equal_dense_matrix_forms():
+    """K, N, S of the oracle == the paper's matrix expressions built densely:
+    K_ab = w^T grad_a grad_b t, N = w^T V_nl t, S_ab = sum_I w^T V^I (X_b - R_Ib) grad_a t (Sec. 4)."""
+    prob, reg = _tiny_region()
+    H = reg.dense_H()
+    lam = np.linalg.eigvalsh(H)
+    lo, hi = lam[0] - 0.3, lam[-1] + 0.2
+    cols = chebyshev_columns(reg, 0.5 * (hi + lo), 0.5 * (hi - lo), 12)
+    G = [reg.dense_grad(a) for a in range(3)]
+    C = reg.chi.toarray()
+    Vnl = C.T @ np.diag(reg.gamma * prob.dV) @ C
+    e = reg.unit().reshape(-1)
+    X = reg.X.reshape(-1, 3)
+    # group projector rows by atom image (identical image position)
+    imgs = {}
+    for r, R in enumerate(reg.R_img):
+        imgs.setdefault(tuple(np.round(R, 12)), []).append(r)
+    for t in cols:
+        tv = t.reshape(-1)
+        mom = reg.moments(t)
+        assert mom[0] == pytest.approx(tv[e.argmax()], abs=1e-15)
+        for slot, (a, b) in enumerate(K_PAIRS):
+            assert abs(mom[1 + slot] - e @ G[a] @ G[b] @ tv) < 1e-10 * (1 + abs(mom[1 + slot]))
+        assert abs(mom[7] - e @ Vnl @ tv) < 1e-12
+        for a in range(3):
+            for b in range(3):
+                s = 0.0
+                for R, rows in imgs.items():
+                    VI = C[rows].T @ np.diag(reg.gamma[rows] * prob.dV) @ C[rows]
+                    s += e @ VI @ ((X[:, b] - R[b]) * (G[a] @ tv))
+                assert abs(mom[8 + 3 * a + b] - s) < 1e-12 * (1 + abs(s))
+
+
+# ---------------------------------------------------------------- P2: Chebyshev vs exact g(H_q)
+def test_p2_density_matrix_column_within_chebyshev_tail():
+    prob, reg = _tiny_region()
+    H = reg.dense_H()
+    lam, U = np.linalg.eigh(H)
+    lo, hi = lam[0] - 0.3, lam[-1] + 0.2
+    chi_q, zeta_q = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    mu, kT = 0.3 * lam[0] + 0.7 * lam[-1], 2.0
+    n_pl = 40
+    cols = chebyshev_columns(reg, chi_q, zeta_q, n_pl)
+    c, _, _ = fd_coefficients(mu, kT, chi_q, zeta_q, n_pl, 2048)
+    approx = sum(wp * cj * t.reshape(-1) for wp, cj, t in zip(primed(n_pl), c, cols))
+    e = reg.unit().reshape(-1)
+    exact = U @ (fermi((lam - mu) / kT) * (U.T @ e))
+    c_long, _, _ = fd_coefficients(mu, kT, chi_q, zeta_q, 400, 4096)
+    tail = np.abs(c_long[n_pl + 1:]).sum()
+    assert np.abs(approx - exact).max() <= tail + 1e-13
+
+
+# ---------------------------------------------------------------- P3: infinite-cell limit
+def test_p3_sq_converges_to_k_integrated_dense_result():
+    """Infinite-cell SQ -> infinite crystal (k-integrated dense diagonalisation, stored by
+    tests/golden/make_golden.py from the oracle only) as R_cut and n_pl grow."""
+    with open(os.path.join(GOLDEN, "p3_dense_k.json")) as f:
+        ref = json.load(f)
+    case = dict(ref["case"])
+    bounds = lanczos_bounds(Problem(tiny_instance(**{**case, "r_cut": 4.5})))
+    errs = []
+    for rc, npl in ((1.8, 20), (2.7, 30), (4.5, 50)):
+        o = run(tiny_instance(**{**case, "r_cut": rc, "n_pl": npl}), bounds=bounds)
+        errs.append(max(abs(o["mu"] - ref["mu"]), abs(o["E_band"] - ref["E_band"]), abs(o["E_s"] - ref["E_s"]),
+                        abs(o["E_nl"] - ref["E_nl"]), np.abs(o["rho"] - np.array(ref["rho"])).max(),
+                        np.abs(o["sigma"] - np.array(ref["sigma"])).max()))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-8
+
+
+# ---------------------------------------------------------------- P4: free electrons
+def test_p4_free_electron_bz_closed_form_and_separable_region():
+    """V = 0, no projectors: SQ density and kinetic stress == Brillouin-zone integrals
+    (paper form uses G(theta)^2 of the first-derivative symbol), and the truncated region ==
+    the exactly separable Kronecker-sum result."""
+    h = 1.0
+    inst = tiny_instance(seed=5, n=(3, 3, 3), h=(h, h, h), n_atoms=0, n_o=2, kT=3.17, r_cut=6.0,
+                         n_pl=40, proj=[], vdepth=0.0, n_e=10.0)
+    inst["proj"] = [[]]
+    prob = Problem(inst)
+    lo, hi = -0.05, 8.2
+    mom = node_moments(prob, np.array([0, 0, 0]), lo, hi)
+    mom_all = np.repeat(mom[None], prob.Nd, axis=0)     # translation invariance
+    mu = fermi_bisect(mom_all[:, :, 0].sum(0), prob.n_e, prob.kT, lo, hi, prob.M)
+    out = contract(prob, mom_all, mu, lo, hi)
+    bz = free_electron.bz_values(mu, prob.kT, prob.h, prob.n_o)
+    assert abs(out["rho"][0] - bz["rho"]) < 1e-9
+    np.testing.assert_allclose(np.diag(out["sigma"]), bz["sigma_paper_diag"], atol=1e-9)
+    assert np.abs(out["sigma"] - np.diag(np.diag(out["sigma"]))).max() < 1e-13
+    assert abs(out["E_band"] / prob.vol - bz["E_band_density"]) < 1e-9
+    assert abs(out["E_s"] / prob.vol - bz["E_s_density"]) < 1e-9
+    # truncated region, exact by separability, against the same Chebyshev sums
+    diag, kin = free_electron.separable_region(lambda e: fermi((e - mu) / prob.kT), prob.h, prob.n_o, prob.m)
+    c, _, _ = fd_coefficients(mu, prob.kT, 0.5 * (hi + lo), 0.5 * (hi - lo), prob.n_pl, prob.M)
+    cw = primed(prob.n_pl) * c
+    assert abs(cw @ mom[:, 0] - diag) < 1e-12
+    np.testing.assert_allclose([cw @ mom[:, 1], cw @ mom[:, 2], cw @ mom[:, 3]], kin, atol=1e-11)
+
+
+# ---------------------------------------------------------------- P5: strain derivative
+def _p5_problem(n=4, n_o=2):
+    L = 3.6
+    return Problem(tiny_instance(seed=1, n=(n, n, n), h=(L / n,) * 3, n_o=n_o, kT=3.17, n_e=2,
+                                 pos=np.array([[0.7, 1.3, 2.2], [2.5, 2.9, 0.4]]),
+                                 proj=[{"l": 0, "width": 0.8, "gamma": 1.0, "rcut": 8.0},
+                                       {"l": 1, "width": 0.8, "gamma": 0.5, "rcut": 8.0}]))
+
+
+def test_p5_strain_finite_difference_equals_density_matrix_stress():
+    """(1/|Omega|) dF/dF_ab of the Mermin free energy under homogeneous strain (Eq.
+    stressdefinition) == 2 tr(D dH/dF_ab)/|Omega| of the same grid Hamiltonian."""
+    prob = _p5_problem()
+    obs = dense_k.observables(prob, nk=2)
+    scale = np.abs(obs["sigma_strain"]).max()
+    for (a, b) in ((0, 0), (0, 1), (2, 1)):
+        fd = dense_k.strain_fd_stress(prob, a, b, nk=2)
+        assert abs(fd - obs["sigma_strain"][a, b]) < 1e-7 * scale
+
+
+def test_p5_paper_nonlocal_stress_converges_to_strain_form():
+    """The paper's discrete sigma^III (summation by parts, (X_b - R_b) grad_a) differs from the
+    strain-consistent form only by discretisation error, which shrinks with h."""
+    diffs = []
+    for n in (4, 6, 8):
+        obs = dense_k.observables(_p5_problem(n=n, n_o=4), nk=2)
+        diffs.append(np.abs(obs["sigma_III"] - obs["sigma_III_strain"]).max())
+    assert diffs[0] > diffs[1] > diffs[2]
+    assert diffs[2] < 0.02 * diffs[0]
+
+
+# ---------------------------------------------------------------- P6-P9 on a small cell
+@pytest.fixture(scope="module")
+def small_run():
+    inst = tiny_instance(seed=11, n=(5, 5, 5), h=(0.8, 0.8, 0.8), n_atoms=3, n_o=3, r_cut=2.4, n_pl=24)
+    prob = Problem(inst)
+    bounds = lanczos_bounds(prob)
+    return inst, bounds, run(inst, bounds=bounds)
+
+
+def test_p6_electron_count(small_run):
+    inst, _, out = small_run
+    assert abs(out["N_check"] - inst["n_e"]) < 1e-12 * inst["n_e"]
+
+
+def _rotate_z(inst):
+    """90 degree rotation about z through the origin: (x, y, z) -> (-y, x, z) on a cubic grid."""
+    n = int(inst["n"][0])
+    L = float(inst["L"][0])
+    v = np.asarray(inst["v_eff"]).reshape(n, n, n)          # [iz, iy, ix]
+    vr = np.empty_like(v)
+    for iy in range(n):
+        for ix in range(n):
+            vr[:, ix, (-iy) % n] = v[:, iy, ix]
+    out = dict(inst)
+    out["v_eff"] = vr.reshape(-1)
+    p = np.asarray(inst["pos"])
+    out["pos"] = np.mod(np.stack([-p[:, 1], p[:, 0], p[:, 2]], axis=1), L)
+    return out
+
+
+def test_p7_rotation_translation_permutation(small_run):
+    inst, bounds, out = small_run
+    Q = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    rot = run(_rotate_z(inst), bounds=bounds)
+    np.testing.assert_allclose(rot["sigma"], Q @ out["sigma"] @ Q.T, atol=1e-12)
+    assert rot["E_band"] == pytest.approx(out["E_band"], abs=1e-11)
+    # translation by one grid vector along y
+    n = int(inst["n"][0])
+    tr = dict(inst)
+    tr["v_eff"] = np.roll(np.asarray(inst["v_eff"]).reshape(n, n, n), 1, axis=1).reshape(-1)
+    tr["pos"] = np.asarray(inst["pos"]) + np.array([0.0, float(inst["L"][1]) / n, 0.0])
+    o2 = run(tr, bounds=bounds)
+    np.testing.assert_allclose(o2["sigma"], out["sigma"], atol=1e-12)
+    np.testing.assert_allclose(np.roll(out["rho"].reshape(n, n, n), 1, axis=1).reshape(-1), o2["rho"], atol=1e-12)
+    # atom permutation
+    pm = dict(inst)
+    pm["pos"] = np.asarray(inst["pos"])[::-1].copy()
+    o3 = run(pm, bounds=bounds)
+    np.testing.assert_allclose(o3["sigma"], out["sigma"], atol=1e-13)
+    # grid asymmetry of sigma^III is small (the continuum form is symmetric)
+    s3 = out["sigma_III"]
+    assert np.abs(s3 - s3.T).max() < 0.05 * np.abs(s3).max() + 1e-12
+
+
+def test_p8_moment_identity(small_run):
+    """-1/2 sum_a [D2_a t^j]_q / h_a^2 = w^T H t^j - V_q rho^j - N^j with
+    w^T H t^j = chi rho^j + zeta (rho^{j+1} + rho^{j-1}) / 2 (Chebyshev identity)."""
+    inst, (lo, hi), _ = small_run
+    prob = Problem(inst)
+    chi_q, zeta_q = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    q = np.array([2, 1, 3])
+    mom, L2 = node_moments(prob, q, lo, hi, with_d2=True)
+    Vq = prob.v[q[2], q[1], q[0]]
+    rho = mom[:, 0]
+    for j in range(0, prob.n_pl):
+        wHt = chi_q * rho[j] + zeta_q * (rho[j + 1] + (rho[j - 1] if j > 0 else rho[1])) / 2.0
+        lhs = -0.5 * L2[j].sum()
+        assert abs(lhs - (wHt - Vq * rho[j] - mom[j, 7])) < 1e-10 * (1 + abs(lhs))
+
+
+def test_p9_no_projectors_gives_zero_nonlocal_stress(small_run):
+    inst, bounds, _ = small_run
+    z = dict(inst)
+    z["proj"] = [[{"l": 0, "width": 0.5, "gamma": 0.0, "rcut": 3.5}]]
+    o = run(z, bounds=bounds)
+    assert abs(o["E_nl"]) < 1e-15
+    assert np.abs(o["sigma_III"]).max() < 1e-15
+
+
+def test_lanczos_bounds_contain_region_spectra():
+    inst = tiny_instance(seed=2, n=(4, 4, 4), h=(0.8, 0.8, 0.8), n_atoms=2, n_o=2, r_cut=1.6, n_pl=10)
+    prob = Problem(inst)
+    lo, hi = lanczos_bounds(prob)
+    for idx in range(prob.Nd):
+        lam = np.linalg.eigvalsh(NodeRegion(prob, prob.node_coords(idx)).dense_H())
+        assert lo <= lam[0] and lam[-1] <= hi
+
+
+def test_config1_instance_shape():
+    inst = make_instance(1)
+    prob = Problem(inst)
+    assert list(prob.m) == [6, 6, 6] and prob.Nc == 13 ** 3 and prob.Nd == 1728
+    assert Problem(make_instance(2)).Nc == 27 ** 3
