@@ -469,23 +469,27 @@ def lanczos_start(nc: int, node_index: int) -> np.ndarray:
 
 
 def lanczos_extremes(apply, v0: np.ndarray, k: int):
-    """Returns (theta_min - res_min, theta_max + res_max) of the k-step Lanczos process."""
+    """k-step Lanczos with full reorthogonalisation by classical Gram-Schmidt applied twice:
+    w = H v_i, c = V^T w, w -= V c, c' = V^T w, w -= V c', alpha_i = c_i + c'_i,
+    beta_i = ||w||, v_{i+1} = w / beta_i (stop early when beta_i <= 1e-12 max(1, |alpha_i|)).
+    Returns (theta_min - res_min, theta_max + res_max) of the tridiagonal (alpha, beta),
+    res = beta_last |last component of the Ritz vector|."""
     V = [v0]
     alpha, beta = [], []
-    w = apply(v0)
     for i in range(k):
-        a = float(np.dot(V[i], w))
-        alpha.append(a)
-        w = w - a * V[i] - (beta[-1] * V[i - 1] if i > 0 else 0.0)
-        for _ in range(2):                      # full reorthogonalisation, twice
-            for u in V:
-                w = w - np.dot(u, w) * u
+        w = apply(V[i])
+        Vm = np.array(V)
+        c1 = Vm @ w
+        w = w - Vm.T @ c1
+        c2 = Vm @ w
+        w = w - Vm.T @ c2
+        a = float(c1[i] + c2[i])
         b = float(np.linalg.norm(w))
+        alpha.append(a)
         beta.append(b)
         if i == k - 1 or b <= 1e-12 * max(1.0, abs(a)):
             break
         V.append(w / b)
-        w = apply(V[-1])
     kk = len(alpha)
     theta, S = scipy.linalg.eigh_tridiagonal(np.array(alpha), np.array(beta[:kk - 1]))
     res = abs(beta[kk - 1]) * np.abs(S[-1, :])
@@ -493,18 +497,30 @@ def lanczos_extremes(apply, v0: np.ndarray, k: int):
 
 
 def lanczos_sample_nodes(prob: Problem):
+    """Seeds argmin V, argmax V and a stride-n/2 node grid; every node of the 2 x 2 x 2 node
+    block (origin at even lattice coordinates) holding a seed is sampled, blocks in order of
+    first appearance, nodes within a block x fastest."""
     v = prob.v.reshape(-1)
-    nodes = [int(np.argmin(v)), int(np.argmax(v))]
+    seeds = [int(np.argmin(v)), int(np.argmax(v))]
     steps = [max(1, int(prob.n[a]) // 2) for a in range(3)]
     for iz in range(0, int(prob.n[2]), steps[2]):
         for iy in range(0, int(prob.n[1]), steps[1]):
             for ix in range(0, int(prob.n[0]), steps[0]):
-                nodes.append(int(ix + prob.n[0] * (iy + prob.n[1] * iz)))
-    out = []
-    for q in nodes:
-        if q not in out:
-            out.append(q)
-    return out
+                seeds.append(int(ix + prob.n[0] * (iy + prob.n[1] * iz)))
+    blocks = []
+    for q in seeds:
+        blk = tuple(int(c) // 2 for c in prob.node_coords(q))
+        if blk not in blocks:
+            blocks.append(blk)
+    nodes = []
+    for blk in blocks:
+        for dz in range(2):
+            for dy in range(2):
+                for dx in range(2):
+                    c = (2 * blk[0] + dx, 2 * blk[1] + dy, 2 * blk[2] + dz)
+                    if all(c[a] < prob.n[a] for a in range(3)):
+                        nodes.append(int(c[0] + prob.n[0] * (c[1] + prob.n[1] * c[2])))
+    return nodes
 
 
 def lanczos_bounds(prob: Problem, k: int = 40):
