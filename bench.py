@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the infinite-cell Clenshaw-Curtis SQ density / energy / stress evaluation.
+
+Workload: 64 H atoms in a 12 bohr periodic cube, h = 0.3 bohr (40^3 nodes), 12th-order
+stencil (n_o = 6), Gaussian V_eff and s+p Kleinman-Bylander projectors, kT = 3.17 Ha,
+R_cut = 4 bohr (27^3 region per node), n_pl = 60 (seeded synthetic input).
+
+One step = one stress evaluation: Lanczos spectral bounds, the per-wave setup (atom-image
+lists, projector weights), the Chebyshev sweep with all moments, the Fermi-level bisection
+and the contraction into rho, energies and sigma - every row of the hot path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference    # the FP64 CPU oracle on the host cores
+
+With N > 1 (torchrun) every rank evaluates its own snapshot (independent instances, no
+data-path collective): weak scaling, value = all ranks' evaluations / max-rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stress evals/s"
+CONFIG_NAME = "64H_12bohr_40cube_no6_sp_rcut4_27cube_npl60_kT3.17"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--fp64-compare", action="store_true",
+                    help="also time one FP64 evaluation (the plain FP64 GPU path) on the same input")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def stencil_traffic(sweep_hash: str):
+    """Per-launch DRAM traffic of the stencil kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if t.get("sweep_source_sha1") == sweep_hash:
+            return float(t["bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def _oracle_nodes(args):
+    inst, nodes, lo, hi = args
+    from oracle import sq_oracle as orc
+    prob = orc.Problem(inst)
+    t0 = time.perf_counter()
+    for q in nodes:
+        orc.node_moments(prob, prob.node_coords(q), lo, hi)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(inst, seconds: float):
+    """The oracle as it stands, node by node on all host cores (spawn pool): evaluations/s
+    extrapolated from a bounded sample of nodes (per-node moments dominate its cost)."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import sq_oracle as orc
+    prob = orc.Problem(inst)
+    lo, hi = -6.0, 130.0
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    orc.node_moments(prob, prob.node_coords(0), lo, hi)
+    per_node = time.perf_counter() - t0
+    per_worker = max(1, int(seconds / max(per_node, 1e-3)))
+    rng = np.random.Generator(np.random.PCG64(12345))
+    nodes = rng.choice(prob.Nd, size=min(prob.Nd, per_worker * cores), replace=False).tolist()
+    chunks = [nodes[i::cores] for i in range(cores)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_nodes, [(inst, ch, lo, hi) for ch in chunks if ch])
+    wall = time.perf_counter() - t0
+    nodes_per_s = len(nodes) / wall
+    return {"value": nodes_per_s / prob.Nd, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{len(nodes)} of {prob.Nd} node columns (moments, n_pl={prob.n_pl}) in {wall:.1f} s "
+                      f"on {cores} processes; Fermi search and contraction (O(N_d n_pl)) not timed",
+            "nodes_per_s": nodes_per_s}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from workloads import make_instance
+    inst = make_instance(args.config)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_oracle_rate(inst, 1.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_rate(inst, max(1.0, args.cpu_seconds / max(1, args.steps))))
+    wall = time.perf_counter() - t0
+    v = sum(x["value"] for x in vals) / len(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": CONFIG_NAME, "flush_l2": "working set > L2 (CPU run)"},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": vals[0]["cores"], "kind": "oracle",
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2006_03697_gb300 import build
+    build.build()
+    from paper_2006_03697_gb300 import sq
+    from workloads import make_instance
+
+    inst = make_instance(args.config, instance=rank)
+    nd = int(np.prod(inst["n"]))
+    prec = sq.SQ_MIXED if args.precision == "mixed" else sq.SQ_FP64
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    desc = sq.Desc(inst, prec, bounds=None, stream=sptr)
+    h = sq.sq_setup(desc)
+    rho_dev = torch.empty(nd, dtype=torch.float64, device="cuda")
+    sig_dev = torch.empty(9, dtype=torch.float64, device="cuda")
+
+    def step():
+        sq.sq_moments(h)
+        mu = sq.sq_fermi_level(h)
+        return sq.sq_density_energy_stress_dev(h, mu, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
+
+    for _ in range(args.warmup):
+        en = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    l0 = sq.sq_kernel_launches(h)
+    sq.sq_kernel_timing(h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        en = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = sq.sq_kernel_launches(h) - l0
+    kern = {}
+    for name, kid in (("stencil", sq.SQ_K_STENCIL), ("project", sq.SQ_K_PROJECT), ("moments", sq.SQ_K_MOMENTS)):
+        n, kms, kb = sq.sq_kernel_timing_read(h, kid)
+        kern[name] = {"launches": n, "ms": kms, "bytes": kb}
+    sq.sq_kernel_timing(h, False)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+
+    # e2e: the public C ABI from host buffers, setup copies and host outputs inside the region
+    rho_h = np.zeros(nd)
+    h2d = desc.v.nbytes + desc.pos.nbytes + desc.species.nbytes + desc.offs.nbytes
+    d2h = rho_h.nbytes + 9 * 8 + 6 * 8
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hh = sq.sq_setup(desc)
+        sq.sq_moments(hh)
+        mu = sq.sq_fermi_level(hh)
+        rho_h, en2, sig_h = sq.sq_density_energy_stress(hh, mu, nd)
+        sq.sq_destroy(hh)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
+
+    # roofline of the dominant sweep kernel
+    hbm, peak_kind = peaks()
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    st = kern["stencil"]
+    sweep_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2006_03697_gb300", "csrc", "sq_sweep.cu"),
+                                   "rb").read()).hexdigest()
+    achieved = (st["bytes"] / st["launches"]) / (st["ms"] / st["launches"] / 1000.0) / 1e9 if st["launches"] else 0.0
+    roof = {"kernel": "k_stencil", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": stencil_traffic(sweep_hash),
+            "peak_source": peak_kind, "dominant_kernel": dom,
+            "algo_bytes_per_launch": st["bytes"] / max(1, st["launches"]),
+            "avg_launch_ms": st["ms"] / max(1, st["launches"])}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == sq.SQ_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": CONFIG_NAME, "precision": args.precision, "bounds": "lanczos (device, per step)",
+                   "node_columns_per_step": nd, "flush_l2": "no flush: per-wave working set (~9 GB) > L2"},
+        "node_columns_per_s": value * nd,
+        "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
+        "kernels": kern, "energies": {k: en[k] for k in ("E_band", "E_s", "E_nl", "F", "N_check", "mu")},
+        "sigma": sig_dev.cpu().numpy().reshape(3, 3).tolist(),
+    }
+    if args.fp64_compare and rank == 0:
+        d64 = sq.Desc(inst, sq.SQ_FP64, bounds=None, stream=sptr)
+        h64 = sq.sq_setup(d64)
+        sq.sq_moments(h64)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        sq.sq_moments(h64)
+        mu64 = sq.sq_fermi_level(h64)
+        en64 = sq.sq_density_energy_stress_dev(h64, mu64, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        f64ms = a0.elapsed_time(a1)
+        line["fp64_gpu"] = {"value": 1000.0 / f64ms, "unit": METRIC, "ms_per_step": f64ms, "steps": 1,
+                            "F": en64["F"], "speedup_of_value": value / (1000.0 / f64ms)}
+        sq.sq_destroy(h64)
+    sq.sq_destroy(h)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rate(inst, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * sq_api.h -- C ABI of the GB300 infinite-cell Clenshaw-Curtis Spectral Quadrature (SQ)
+ * library: electron density, band / entropy / nonlocal energies and the density-matrix
+ * (kinetic + nonlocal) Hellmann-Feynman stress of an orthorhombic periodic cell, following
+ * Sharma, Hamel, Bethkenhagen, Pask, Suryanarayana, "Real-space formulation of the stress
+ * tensor for O(N) density functional theory" (arXiv 2006.03697), Sec. 4 and App. A.
+ *
+ * Problem statement (Sec. 4). The cell is discretised by a uniform grid K_Omega of N_d nodes,
+ * node i at (ix h0, iy h1, iz h2), h_a = L_a / n_a. For every node q the nodal Hamiltonian
+ * H_q is the restriction of the infinite-crystal grid Hamiltonian
+ *     H = -1/2 Lap_h + V_eff + sum_{I in R^3} sum_lm gamma_Jl |dOmega| chi_Ilm chi_Ilm^T
+ * to the node's region of influence, the cube of half-width R_cut around q
+ * (m_a = floor(R_cut / h_a + 1e-9) points per side, zero extension outside it).
+ * With Hhat_q = (H_q - chi I) / zeta and the Chebyshev columns
+ *     t^0 = e_q,  t^1 = Hhat_q e_q,  t^{j+1} = 2 Hhat_q t^j - t^{j-1}   (j < n_pl),
+ * the library forms per node and per j = 0..n_pl the moments
+ *     rho^j = e_q^T t^j,  K^j_ab = e_q^T grad_a,q grad_b,q t^j,  N^j = e_q^T V_nl,q t^j,
+ *     S^j_ab = sum_I e_q^T V^I_nl,q (X_b,q - R_Ib) grad_a,q t^j,
+ * finds the Fermi level mu from N_e = 2 sum_q sum'_j c^j(mu) rho_q^j, and contracts
+ *     rho_q  = (2/|dOmega|) sum'_j c^j rho_q^j
+ *     E_band = 2 sum_q sum'_j (chi c^j + zeta d^j) rho_q^j          (App. A)
+ *     E_s    = 2 kT sum_q sum'_j s^j rho_q^j      (-TS; s = g ln g + (1-g) ln(1-g))
+ *     E_nl   = 2 sum_q sum'_j c^j N_q^j
+ *     sigma  = [2 sum sum' c^j K^j - 2 sum sum' c^j (delta N^j + 2 S^j)] / |Omega|
+ * where c^j, d^j, s^j are the Chebyshev coefficients of the Fermi-Dirac function g, of r g(r)
+ * and of the entropy function in the scaled variable, and the primed sum halves j = 0.
+ *
+ * Conventions
+ *   - Units: Hartree atomic units (Ha, bohr); spin-unpolarised (factor 2).
+ *   - Arrays are row-major; grid arrays are x fastest: i = ix + n0 (iy + n1 iz).
+ *   - sigma is returned row-major 3x3 in Ha/bohr^3 (sigma[3*a + b]).
+ *   - Every call returns an int status (SQ_OK = 0). The library never aborts or traps; on
+ *     error sq_last_error() describes the failure. Device waits are bounded and report
+ *     SQ_ERR_TIMEOUT.
+ *   - The caller owns every host buffer passed in or out; the library copies inputs during
+ *     sq_setup and owns all device memory of a handle until sq_destroy.
+ *   - A handle is used by one host thread at a time. Work is issued on desc->stream
+ *     (a cudaStream_t; NULL selects the legacy default stream).
+ */
+#ifndef SQ_API_H
+#define SQ_API_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SQ_OK 0
+#define SQ_ERR_INVALID_ARG 1   /* a descriptor field or pointer is out of range       */
+#define SQ_ERR_OOM 2           /* device or host allocation failed                    */
+#define SQ_ERR_CUDA 3          /* a CUDA runtime call failed                           */
+#define SQ_ERR_NO_BRACKET 4    /* N(mu) - N_e has no sign change on the bisection bracket */
+#define SQ_ERR_TIMEOUT 5       /* a bounded device wait gave up                        */
+#define SQ_ERR_STATE 6         /* call out of order (e.g. contraction before moments)  */
+
+/* precision modes */
+#define SQ_FP64 0    /* FP64 recurrence, projectors and moments                          */
+#define SQ_MIXED 1   /* FP32 recurrence / projectors / moment products, FP64 node sums,
+                        FP64 bounds, coefficients, bisection and contraction            */
+
+/* spectral bound modes (the paper takes chi, zeta from the extreme eigenvalues of H_q) */
+#define SQ_BOUNDS_LANCZOS 0   /* k-step Lanczos on sample regions, widened (default)   */
+#define SQ_BOUNDS_GIVEN 1     /* lambda_lo / lambda_hi taken from the descriptor        */
+
+/* Moments per node and Chebyshev index (sq_moments_copy layout) */
+#define SQ_N_MOMENTS 17  /* rho, K_xx K_yy K_zz K_yz K_xz K_xy, N, S_ab (8 + 3a + b) */
+
+/* Gaussian Kleinman-Bylander projector of one species (stand-in for the pseudopotential
+ * projectors chi_Jlm of Eqs. sigmaIII / E_nl):
+ *   l = 0: chi = (pi w^2)^(-3/4) exp(-r^2 / (2 w^2))
+ *   l = 1: chi_m = sqrt(2)/w * d_m * (pi w^2)^(-3/4) exp(-r^2 / (2 w^2)),  m = x, y, z
+ * zero for r > rcut (rcut <= 0 selects 7 w). */
+typedef struct {
+  int l;          /* 0 or 1                                     */
+  double width;   /* w > 0 (bohr)                               */
+  double gamma;   /* gamma_Jl (Ha)                              */
+  double rcut;    /* support radius (bohr)                      */
+} sq_proj;
+
+typedef struct {
+  double L[3];                 /* orthorhombic cell sides (bohr), > 0                          */
+  int n[3];                    /* nodes per side, >= 1                                          */
+  int n_o;                     /* FD half-order 1..6 (2 n_o-order central stencils)            */
+  const double* v_eff;         /* host, N_d values (x fastest), finite                          */
+  int n_atoms;                 /* >= 0                                                          */
+  const double* pos;           /* host, [n_atoms][3] bohr, any real values (periodic)           */
+  const int* species;          /* host, [n_atoms] in [0, n_species)                             */
+  int n_species;               /* >= 1 when n_atoms > 0                                         */
+  const int* proj_offset;      /* host, [n_species + 1]: projectors of species s are
+                                  proj[proj_offset[s] .. proj_offset[s+1])                      */
+  const sq_proj* proj;         /* host, [proj_offset[n_species]]                                */
+  double kT;                   /* smearing sigma = kT > 0 (Ha)                                  */
+  double n_e;                  /* electrons per cell, 0 < n_e < 2 N_d                           */
+  double r_cut;                /* truncation radius (bohr); m_a >= 1 required                   */
+  int n_pl;                    /* Chebyshev degree >= 1 (terms j = 0..n_pl)                     */
+  int precision;               /* SQ_FP64 | SQ_MIXED                                            */
+  int bounds_mode;             /* SQ_BOUNDS_LANCZOS | SQ_BOUNDS_GIVEN                           */
+  double lambda_lo, lambda_hi; /* used with SQ_BOUNDS_GIVEN; lambda_lo < lambda_hi               */
+  int cheb_quad_M;             /* Chebyshev-Gauss points for c, d, s (<= 0 selects 2048)        */
+  int lanczos_k;               /* Lanczos steps (<= 0 selects 40)                               */
+  void* stream;                /* cudaStream_t or NULL                                          */
+} sq_instance_desc;
+
+typedef struct {
+  double E_band;   /* 2 sum_q sum' (chi c + zeta d) rho^j  (Ha)      */
+  double E_s;      /* -TS (Ha)                                       */
+  double E_nl;     /* nonlocal energy (Ha)                           */
+  double F;        /* E_band + E_s (Mermin free energy of these terms) */
+  double N_check;  /* |dOmega| sum_q rho_q (should equal n_e)        */
+  double mu;       /* Fermi level used (Ha)                          */
+} sq_energies;
+
+typedef struct sq_handle sq_handle;
+
+/* Validates desc, copies every input to the device, samples the projectors on their support
+ * boxes, builds the per-tile atom-image lists and allocates the recurrence buffers.
+ * On success *out owns all device memory of the instance. Errors: SQ_ERR_INVALID_ARG,
+ * SQ_ERR_OOM, SQ_ERR_CUDA (then *out is NULL). */
+int sq_setup(const sq_instance_desc* desc, sq_handle** out);
+
+/* Spectral bounds (SQ_BOUNDS_LANCZOS: device Lanczos, Sec. 4 chi_q / zeta_q), then the
+ * Chebyshev sweep over every node (Sec. 4 three-term recurrence) and the moment table.
+ * Asynchronous on the handle's stream. Errors: SQ_ERR_CUDA, SQ_ERR_TIMEOUT. */
+int sq_moments(sq_handle* h);
+
+/* Fermi level by FP64 bisection on N(mu) = 2 sum'_j c^j(mu) R^j, R^j = sum_q rho_q^j, on
+ * [lambda_lo - 40 kT, lambda_hi + 40 kT] until the bracket is < 1e-13 max(1, |mu|) or 200
+ * steps; runs on the device and synchronises the stream. Errors: SQ_ERR_STATE (no moments),
+ * SQ_ERR_NO_BRACKET, SQ_ERR_CUDA. */
+int sq_fermi_level(sq_handle* h, double* mu_out);
+
+/* Contraction at mu (Sec. 4 rho_q and stress sums, App. A band energy). Host outputs:
+ * rho_out [N_d] or NULL, e_out or NULL, sigma_out [9] or NULL. Synchronises the stream. */
+int sq_density_energy_stress(sq_handle* h, double mu, double* rho_out, sq_energies* e_out,
+                             double* sigma_out);
+
+/* Same with DEVICE outputs (e.g. torch data_ptr): rho_dev [N_d] doubles or NULL, sigma_dev [9]
+ * doubles or NULL; energies (if e_out) are still written to host memory. Does not synchronise
+ * unless e_out is non-NULL. */
+int sq_density_energy_stress_dev(sq_handle* h, double mu, double* rho_dev, sq_energies* e_out,
+                                 double* sigma_dev);
+
+/* Bounds in use (after sq_moments in Lanczos mode). */
+int sq_get_bounds(const sq_handle* h, double* lambda_lo, double* lambda_hi);
+
+/* Copies the moment table [N_d][n_pl + 1][SQ_N_MOMENTS] (FP64, host) for inspection. */
+int sq_moments_copy(sq_handle* h, double* host_out);
+
+/* Device bytes sq_setup would allocate for desc (0 if desc is invalid); used for admission. */
+size_t sq_footprint_bytes(const sq_instance_desc* desc);
+
+/* Number of CUDA kernels the handle launched since sq_setup (all calls). */
+long long sq_kernel_launches(const sq_handle* h);
+
+/* Kernel classes of the Chebyshev sweep timed by sq_kernel_timing (see below). */
+#define SQ_K_STENCIL 0   /* H t^j, window mask, recurrence update, S partials          */
+#define SQ_K_PROJECT 1   /* chi^T t^{j+1} per atom image                                */
+#define SQ_K_MOMENTS 2   /* rho^j, K^j, N^j, S^j per node                               */
+
+/* enable != 0: record a CUDA event pair on the handle's stream around every launch of the
+ * sweep kernels of later sq_moments calls and reset the accumulators; enable == 0: stop. */
+int sq_kernel_timing(sq_handle* h, int enable);
+
+/* For kernel class kid: launches timed, their summed event time (ms), and the algorithmic
+ * bytes they moved (stencil only: 4 B per float / 8 B per double for each read of t^j and
+ * t^{j-1} and each write of t^{j+1}, per node and region point; 0 for other classes). */
+int sq_kernel_timing_read(const sq_handle* h, int kid, long long* launches, double* total_ms,
+                          double* algo_bytes);
+
+void sq_destroy(sq_handle* h);
+
+/* Last error text of h (or of the last failed sq_setup when h is NULL); never NULL. */
+const char* sq_last_error(const sq_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQ_API_H */

@@ -1,0 +1,82 @@
+// Device-side helpers shared by the SQ kernels.
+#pragma once
+
+#include "sq_internal.h"
+
+namespace sq {
+
+__device__ __forceinline__ int floor_div_d(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int ceil_div_d(int a, int b) { return -floor_div_d(-a, b); }
+
+// Tile t (global index) -> origin of its first node in lattice coordinates.
+__device__ __forceinline__ void tile_origin(const Geo& g, int t, int o[3]) {
+  o[0] = (t % g.tiles[0]) * g.b;
+  o[1] = ((t / g.tiles[0]) % g.tiles[1]) * g.b;
+  o[2] = (t / (g.tiles[0] * g.tiles[1])) * g.b;
+}
+
+__device__ __forceinline__ int wave_tile(const Wave& w, int tl) { return w.ids ? w.ids[tl] : w.tile0 + tl; }
+
+// Node slot q of a tile -> offsets inside the tile.
+__device__ __forceinline__ void node_offset(const Geo& g, int q, int qo[3]) {
+  qo[0] = q % g.b;
+  qo[1] = (q / g.b) % g.b;
+  qo[2] = q / (g.b * g.b);
+}
+
+__device__ __forceinline__ bool node_valid(const Geo& g, const int o[3], const int qo[3]) {
+  return o[0] + qo[0] < g.n[0] && o[1] + qo[1] < g.n[1] && o[2] + qo[2] < g.n[2];
+}
+
+// Is U-local point (ux, uy, uz) inside the window of the node with offsets qo?
+__device__ __forceinline__ bool in_window(const Geo& g, const int qo[3], int ux, int uy, int uz) {
+  return (unsigned)(ux - qo[0]) <= (unsigned)(2 * g.m[0]) &&
+         (unsigned)(uy - qo[1]) <= (unsigned)(2 * g.m[1]) &&
+         (unsigned)(uz - qo[2]) <= (unsigned)(2 * g.m[2]);
+}
+
+// Linear index of an absolute lattice point inside an atom image's support box, or -1.
+__device__ __forceinline__ int box_index(const AtomTab& at, const int s[3], const int n[3],
+                                         int ax, int ay, int az) {
+  int lx = ax - s[0] * n[0] - at.lo[0];
+  int ly = ay - s[1] * n[1] - at.lo[1];
+  int lz = az - s[2] * n[2] - at.lo[2];
+  if ((unsigned)lx >= (unsigned)at.dim[0] || (unsigned)ly >= (unsigned)at.dim[1] ||
+      (unsigned)lz >= (unsigned)at.dim[2])
+    return -1;
+  return (lz * at.dim[1] + ly) * at.dim[0] + lx;
+}
+
+// Exclusive block-wide scan of one int per thread (blockDim.x a multiple of 32, <= 1024).
+// Deterministic; returns the exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int warp_sums[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < nw) ? warp_sums[lane] : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    warp_sums[lane] = w;   // inclusive
+  }
+  __syncthreads();
+  int excl = x - v + (warp > 0 ? warp_sums[warp - 1] : 0);
+  *total = warp_sums[nw - 1];
+  __syncthreads();
+  return excl;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+}  // namespace sq

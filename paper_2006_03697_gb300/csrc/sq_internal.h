@@ -1,0 +1,205 @@
+// Internal declarations of the GB300 SQ library (not part of the C ABI).
+//
+// Device layout (node-batched lattice tiles)
+//   * The N_d grid nodes are grouped into tiles of b x b x b adjacent nodes (B = b^3).
+//   * A tile's union window U is the box of absolute (unwrapped) lattice points
+//     [o - m, o + b - 1 + m] per axis (o = tile origin); every node window W_q of the tile
+//     is a sub-box of U. A Chebyshev column t_q^j of every node of the tile is stored on U,
+//     node index innermost: T[pt][node], pt = (uz * Uy + uy) * Ux + ux. Entries outside the
+//     node's own window are held at exactly zero, which realises the restriction H_q of
+//     Sec. 4 (zero extension) while the B nodes share each stencil load of V_eff and of the
+//     projector tables.
+//   * Atoms: each atom's projector channels are sampled once on the atom's support box in
+//     absolute lattice coordinates; a periodic image is the same table shifted by s * n.
+//   * Per tile, the atom images whose support box meets U are listed (TileEntry), and per
+//     4x4x4 brick of U the entries meeting the brick (used by the per-point nonlocal apply).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/sq_api.h"
+
+namespace sq {
+
+constexpr int kMaxNo = 6;        // largest FD half-order supported
+constexpr int kBrick = 4;        // brick side in points
+constexpr int kMaxCh = 8;        // projector channels per atom
+constexpr int kThreads = 256;    // block size of the tile kernels
+
+struct AtomTab {
+  int lo[3];        // support box corner (absolute lattice coordinates of the base image)
+  int dim[3];       // support box extent
+  int nch;          // channels
+  int ch0;          // first channel in the per-channel arrays
+  long long off;    // offset of channel 0 in the table array; channel c at off + c * boxpts
+  double R[3];      // base image position (wrapped into the cell)
+};
+
+struct TileEntry {
+  int atom;         // atom index
+  int s[3];         // image shift in cells
+  int row0;         // first projector row of this entry in the tile's P / A arrays
+  int pad;
+};
+
+// Everything a tile kernel needs, passed by value.
+struct Geo {
+  int n[3];
+  int m[3];
+  int b, B;
+  int U[3];
+  int Upts;
+  int nbr[3];       // bricks per axis
+  int nbricks;
+  int tiles[3];
+  int n_tiles;
+  int n_o;
+  int n_atoms;
+  double h[3];
+  double L[3];
+  double dV;
+  double lap0;                    // -1/2 sum_a w0 / h_a^2
+  double lap[3][kMaxNo + 1];      // -1/2 w_p / h_a^2
+  double grd[3][kMaxNo + 1];      // g_p / h_a
+  int e_cap;                      // entries per tile (capacity)
+  int r_cap;                      // projector rows per tile (capacity)
+  int br_cap;                     // entries per brick (capacity)
+  int n_pl;
+  int nslab;                      // z-slabs of kBrick planes per tile
+};
+
+struct Wave {
+  int tile0;           // first global tile of this wave (when ids is null)
+  int ntiles;          // tiles in this wave
+  const int* ids;      // device list of global tile indices, or null for tile0 + i
+};
+
+// Per-wave device buffers (sized for the largest wave).
+struct WaveBufs {
+  TileEntry* entries = nullptr;   // [wt][e_cap]
+  int* n_entries = nullptr;       // [wt]
+  int* n_rows = nullptr;          // [wt]
+  int* brick_list = nullptr;      // [wt][nbricks][br_cap]
+  int* brick_n = nullptr;         // [wt][nbricks]
+  void* T[3] = {nullptr, nullptr, nullptr};   // Real [wt][Upts][B]
+  void* W = nullptr;              // Real [wt][3][Upts][B]
+  void* A = nullptr;              // Real [wt][r_cap][B]
+  void* P = nullptr;              // Real [wt][r_cap][B]
+  double* Spart = nullptr;        // [wt][nslab][B][9]
+};
+
+struct Dev {
+  double* v64 = nullptr;          // V_eff (N_d)
+  float* v32 = nullptr;
+  AtomTab* atoms = nullptr;       // [n_atoms]
+  double* gdv = nullptr;          // gamma * dV per channel
+  double* chi64 = nullptr;        // projector tables
+  float* chi32 = nullptr;
+  double* mom = nullptr;          // [N_d][n_pl+1][17]
+  double* R = nullptr;            // [n_pl+1] node sums of rho^j
+  double* cosF = nullptr;         // [M] sum'_j cos(j theta_k) R^j
+  double* coef = nullptr;         // [3][n_pl+1] c, d, s at the last contraction mu
+  double* scal = nullptr;         // scalars: mu, bounds, partial sums ...
+  double* part = nullptr;         // contraction partials
+  double* rho = nullptr;          // [N_d]
+  int* status = nullptr;          // device status words
+  double* lzV = nullptr;          // Lanczos basis [(k+1)][nst][Upts][B]
+  double* lzW = nullptr;          // Lanczos work vector [nst][Upts][B]
+  double* lzP = nullptr;          // projections of the Lanczos vector [nst][r_cap][B]
+  double* lzC = nullptr;          // Gram-Schmidt coefficients / alpha, beta [cols][...]
+  int* lz_tiles = nullptr;        // sample tile ids [nst]
+};
+
+}  // namespace sq
+
+struct sq_handle {
+  sq_instance_desc desc;          // copy (host pointers cleared after setup)
+  sq::Geo geo;
+  int precision = SQ_FP64;
+  int bounds_mode = SQ_BOUNDS_LANCZOS;
+  int M = 2048;
+  int lanczos_k = 40;
+  double kT = 0, n_e = 0;
+  double lam_lo = 0, lam_hi = 0;   // effective bounds (those the recurrence realises)
+  double lap_offset = 0;            // constant-mode eigenvalue of the stored stencil weights
+  double hscal[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  bool bounds_ready = false;
+  bool moments_ready = false;
+  int Nd = 0;
+  double vol = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<sq::AtomTab> atoms_h;
+  long long table_len = 0;
+  int n_ch_total = 0;
+  std::vector<sq::Wave> waves;
+  int wave_cap = 0;
+  sq::Dev d;
+  sq::WaveBufs wb;
+  std::vector<int> lanczos_tiles;
+  long long launches = 0;
+  // optional event timing of the sweep kernels
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, double>> ev_pending;   // (kernel class, algorithmic bytes) per pair
+  long long t_launches[3] = {0, 0, 0};
+  double t_ms[3] = {0, 0, 0};
+  double t_bytes[3] = {0, 0, 0};
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace sq {
+
+// Spectral scaling of the recurrence from bounds [lo, hi] (sq_api.cu): writes the step
+// coefficients and the effective bounds used by the Fermi search and the contraction.
+int set_bounds(sq_handle* h, double lo, double hi);
+
+// error helpers
+int fail(sq_handle* h, int code, const std::string& msg);
+#define SQ_CUDA_TRY(h, call)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return ::sq::fail((h), SQ_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+#define SQ_LAUNCH_CHECK(h)                                                                \
+  do {                                                                                    \
+    (h)->launches++;                                                                      \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess)                                                                \
+      return ::sq::fail((h), SQ_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+int dev_alloc(sq_handle* h, void** p, size_t bytes);
+// event timing helpers (sq_api.cu): open a pair before a launch, collect after a sync
+cudaEvent_t timing_begin(sq_handle* h, int kid, double bytes);
+void timing_end(sq_handle* h, cudaEvent_t start);
+int timing_collect(sq_handle* h);
+
+// setup kernels (sq_setup.cu)
+int build_tables(sq_handle* h);
+int build_wave_lists(sq_handle* h, const Wave& w);
+
+// sweep (sq_sweep.cu)
+int run_sweep(sq_handle* h);
+// out = H_q v for every node column of the wave's tiles (FP64), P = projection scratch
+int launch_apply_h64(sq_handle* h, const Wave& w, const double* v, double* out, double* P);
+// entries / brick lists of a wave only (no A, W, t^0)
+int build_wave_entries(sq_handle* h, const Wave& w);
+
+// bounds / Fermi level / contraction (sq_reduce.cu)
+int run_lanczos(sq_handle* h);
+int run_fermi(sq_handle* h, double* mu_out);
+int run_contraction(sq_handle* h, double mu, double* rho_dev, double* sums_host);
+
+// status word indices
+enum StatusWord { kStOverflow = 0, kStNoBracket = 1, kStTimeout = 2, kStCount = 4 };
+
+}  // namespace sq

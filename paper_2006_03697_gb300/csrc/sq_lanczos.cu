@@ -1,0 +1,262 @@
+// Spectral bounds for the Chebyshev scaling chi_q, zeta_q of Sec. 4 (FP64).
+//
+// The paper takes chi_q and zeta_q from the extreme eigenvalues of H_q and does not say how
+// they are obtained. Here: k-step Lanczos on the nodal Hamiltonian H_q of every node of a few
+// sample tiles (one Lanczos column per node, all columns advanced together with the tile
+// kernels), full reorthogonalisation by classical Gram-Schmidt applied twice, Ritz extremes
+// of the tridiagonal matrix widened by their residual norms, the interval over all columns,
+// then widened by 1 % of its width on each side. One interval serves every node (every H_q
+// is a principal submatrix of the infinite-crystal H, so a shared interval is valid for all
+// of them when it contains the sampled spectra with margin).
+#include "sq_device.cuh"
+
+namespace sq {
+
+// Start vector of the column of node q: 1 + (hash(i, node) mod 1009) / 1009 on the window
+// (i = window-local index, C order z, y, x), zero elsewhere; normalised afterwards.
+__global__ void k_lz_init(Geo g, Wave w, double* __restrict__ V0) {
+  const size_t per_tile = (size_t)g.Upts * g.B;
+  const size_t total = per_tile * w.ntiles;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int tl = int(idx / per_tile);
+    const int r = int(idx % per_tile);
+    const int q = r % g.B, pt = r / g.B;
+    const int ux = pt % g.U[0], uy = (pt / g.U[0]) % g.U[1], uz = pt / (g.U[0] * g.U[1]);
+    int o[3], qo[3];
+    tile_origin(g, wave_tile(w, tl), o);
+    node_offset(g, q, qo);
+    double v = 0.0;
+    if (node_valid(g, o, qo) && in_window(g, qo, ux, uy, uz)) {
+      const int kx = ux - qo[0], ky = uy - qo[1], kz = uz - qo[2];
+      const unsigned long long i = (unsigned long long)((kz * (2 * g.m[1] + 1) + ky) * (2 * g.m[0] + 1) + kx);
+      const unsigned long long node =
+          (unsigned long long)((o[0] + qo[0]) + g.n[0] * ((o[1] + qo[1]) + g.n[1] * (o[2] + qo[2])));
+      const unsigned long long hsh = (i * 2654435761ull + node * 40503ull) & 0xFFFFFFFFull;
+      v = 1.0 + double(hsh % 1009ull) / 1009.0;
+    }
+    V0[idx] = v;
+  }
+}
+
+// out[col * ld + i] = <V_i, x>_col for i < nvec (one block per (i, tile); fixed-order sums)
+__global__ void k_lz_dots(Geo g, Wave w, const double* __restrict__ V, int nvec, size_t vstride,
+                          const double* __restrict__ x, double* __restrict__ out, int ld) {
+  const int i = blockIdx.x, tl = blockIdx.y;
+  const size_t base = (size_t)tl * g.Upts * g.B;
+  const double* Vi = V + (size_t)i * vstride + base;
+  const double* xt = x + base;
+  const int q = threadIdx.x % g.B;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < g.Upts * g.B; e += blockDim.x) s += Vi[e] * xt[e];
+  __shared__ double red[kThreads];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < g.B) {
+    double t = 0.0;
+    for (int th = q; th < kThreads; th += g.B) t += red[th];
+    out[((size_t)tl * g.B + q) * ld + i] = t;
+  }
+}
+
+// x -= sum_i coef[col * ld + i] V_i
+__global__ void k_lz_update(Geo g, Wave w, const double* __restrict__ V, int nvec, size_t vstride,
+                            const double* __restrict__ coef, int ld, double* __restrict__ x) {
+  const size_t per_tile = (size_t)g.Upts * g.B;
+  const size_t total = per_tile * w.ntiles;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int tl = int(idx / per_tile);
+    const int q = int(idx % per_tile) % g.B;
+    const double* c = coef + ((size_t)tl * g.B + q) * ld;
+    double acc = 0.0;
+    for (int i = 0; i < nvec; ++i) acc += c[i] * V[(size_t)i * vstride + idx];
+    x[idx] -= acc;
+  }
+}
+
+// Per column: alpha_i = cA_i + cB_i, beta_i = ||w||; a column whose beta falls below
+// 1e-12 max(1, |alpha_i|) stops with k_eff = i + 1 (keff < 0 while running).
+__global__ void k_lz_step(int ncols, int i, int kk, int k, const double* __restrict__ cA, const double* __restrict__ cB,
+                          int ld, const double* __restrict__ nrm, double* __restrict__ alpha, double* __restrict__ beta,
+                          int* __restrict__ keff) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncols || keff[col] >= 0) return;
+  const double a = cA[(size_t)col * ld + i] + cB[(size_t)col * ld + i];
+  const double b = sqrt(nrm[(size_t)col * ld]);
+  alpha[(size_t)col * k + i] = a;
+  beta[(size_t)col * k + i] = b;
+  if (i == kk - 1 || b <= 1e-12 * fmax(1.0, fabs(a))) keff[col] = i + 1;
+}
+
+// V_next = x / beta for running columns (zero otherwise). With first != 0: normalise the
+// start vector in place (beta = sqrt(nrm)); a zero start vector marks an empty column.
+__global__ void k_lz_scale(Geo g, Wave w, const double* __restrict__ x, const double* __restrict__ nrm, int ld,
+                           int* __restrict__ keff, double* __restrict__ Vn, int first) {
+  const size_t per_tile = (size_t)g.Upts * g.B;
+  const size_t total = per_tile * w.ntiles;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int tl = int(idx / per_tile);
+    const int q = int(idx % per_tile) % g.B;
+    const size_t col = (size_t)tl * g.B + q;
+    const double b = sqrt(nrm[col * ld]);
+    const bool run = first ? (b > 0.0) : (keff[col] < 0);
+    Vn[idx] = run ? x[idx] / b : 0.0;
+  }
+}
+
+__global__ void k_lz_mark_empty(int ncols, const double* __restrict__ nrm, int ld, int* __restrict__ keff) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col < ncols) keff[col] = (nrm[(size_t)col * ld] > 0.0) ? -1 : 0;
+}
+
+// Sturm count of eigenvalues of the tridiagonal (a, b) below x.
+__device__ int sturm_count(const double* a, const double* b, int n, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < n; ++i) {
+    d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// |last component| of the unit eigenvector for the extreme eigenvalue theta, by two steps
+// of inverse iteration with the shift just outside the spectrum (definite, so the
+// unpivoted tridiagonal solve is stable).
+__device__ double last_component(const double* a, const double* b, int n, double shift, double* y, double* dd) {
+  for (int i = 0; i < n; ++i) y[i] = 1.0;
+  for (int it = 0; it < 3; ++it) {
+    // LDL^T of (T - shift I), then solve
+    dd[0] = a[0] - shift;
+    for (int i = 1; i < n; ++i) dd[i] = a[i] - shift - b[i - 1] * b[i - 1] / dd[i - 1];
+    for (int i = 1; i < n; ++i) y[i] -= b[i - 1] / dd[i - 1] * y[i - 1];
+    y[n - 1] /= dd[n - 1];
+    for (int i = n - 2; i >= 0; --i) y[i] = (y[i] - b[i] * y[i + 1]) / dd[i];
+    double nr = 0.0;
+    for (int i = 0; i < n; ++i) nr += y[i] * y[i];
+    nr = sqrt(nr);
+    for (int i = 0; i < n; ++i) y[i] /= nr;
+  }
+  return fabs(y[n - 1]);
+}
+
+constexpr int kMaxLanczos = 128;
+
+// One block: Ritz extremes with residual bounds per column, min / max over columns,
+// widening by 1 % of the width; writes scal[8] = lo, scal[9] = hi.
+__global__ void k_lz_bounds(int ncols, int k, const double* __restrict__ alpha, const double* __restrict__ beta,
+                            const int* __restrict__ keff, double* __restrict__ scal) {
+  __shared__ double slo[256], shi[256];
+  double lo = INFINITY, hi = -INFINITY;
+  double y[kMaxLanczos], dd[kMaxLanczos];
+  for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+    const int n = keff[col];
+    if (n <= 0) continue;
+    const double* a = alpha + (size_t)col * k;
+    const double* b = beta + (size_t)col * k;
+    double gl = INFINITY, gu = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < n - 1 ? fabs(b[i]) : 0.0);
+      gl = fmin(gl, a[i] - r);
+      gu = fmax(gu, a[i] + r);
+    }
+    double l = gl, u = gu;                      // smallest eigenvalue: count(x) >= 1
+    for (int it = 0; it < 200 && u - l > 1e-15 * fmax(1.0, fmax(fabs(l), fabs(u))); ++it) {
+      const double mid = 0.5 * (l + u);
+      if (sturm_count(a, b, n, mid) >= 1) u = mid; else l = mid;
+    }
+    const double tmin = 0.5 * (l + u);
+    l = gl; u = gu;                             // largest eigenvalue: count(x) == n
+    for (int it = 0; it < 200 && u - l > 1e-15 * fmax(1.0, fmax(fabs(l), fabs(u))); ++it) {
+      const double mid = 0.5 * (l + u);
+      if (sturm_count(a, b, n, mid) >= n) u = mid; else l = mid;
+    }
+    const double tmax = 0.5 * (l + u);
+    const double bl = fabs(b[n - 1]);
+    const double del = 1e-10 * fmax(gu - gl, 1e-300);
+    const double rmin = (n > 1) ? bl * last_component(a, b, n, tmin - del, y, dd) : bl;
+    const double rmax = (n > 1) ? bl * last_component(a, b, n, tmax + del, y, dd) : bl;
+    lo = fmin(lo, tmin - rmin);
+    hi = fmax(hi, tmax + rmax);
+  }
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double wdt = shi[0] - slo[0];
+    scal[8] = slo[0] - 0.01 * wdt;
+    scal[9] = shi[0] + 0.01 * wdt;
+  }
+}
+
+int run_lanczos(sq_handle* h) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  const int nst = int(h->lanczos_tiles.size());
+  const int k = h->lanczos_k;
+  // never more steps than the region has dimensions (the Krylov space is exhausted)
+  const long long nc = (long long)(2 * g.m[0] + 1) * (2 * g.m[1] + 1) * (2 * g.m[2] + 1);
+  const int kk = int(std::min<long long>(k, nc));
+  const int ncols = nst * g.B;
+  const int ld = k + 1;
+  const Wave w{0, nst, h->d.lz_tiles};
+  const size_t vstride = (size_t)nst * g.Upts * g.B;
+  double* V = h->d.lzV;
+  double* W = h->d.lzW;
+  double* cA = h->d.lzC;
+  double* cB = cA + (size_t)ncols * ld;
+  double* nrm = cB + (size_t)ncols * ld;
+  double* alpha = nrm + (size_t)ncols * ld;
+  double* beta = alpha + (size_t)ncols * k;
+  int* keff = (int*)(beta + (size_t)ncols * k);
+  const int eb = 1024;
+  const int cb = (ncols + 127) / 128;
+  int rc = build_wave_entries(h, w);
+  if (rc != SQ_OK) return rc;
+  k_lz_init<<<eb, 256, 0, s>>>(g, w, V);
+  SQ_LAUNCH_CHECK(h);
+  k_lz_dots<<<dim3(1, nst), kThreads, 0, s>>>(g, w, V, 1, vstride, V, nrm, ld);
+  SQ_LAUNCH_CHECK(h);
+  k_lz_mark_empty<<<cb, 128, 0, s>>>(ncols, nrm, ld, keff);
+  SQ_LAUNCH_CHECK(h);
+  k_lz_scale<<<eb, 256, 0, s>>>(g, w, V, nrm, ld, keff, V, 1);
+  SQ_LAUNCH_CHECK(h);
+  for (int i = 0; i < kk; ++i) {
+    double* Vi = V + (size_t)i * vstride;
+    rc = launch_apply_h64(h, w, Vi, W, h->d.lzP);
+    if (rc != SQ_OK) return rc;
+    k_lz_dots<<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cA, ld);
+    SQ_LAUNCH_CHECK(h);
+    k_lz_update<<<eb, 256, 0, s>>>(g, w, V, i + 1, vstride, cA, ld, W);
+    SQ_LAUNCH_CHECK(h);
+    k_lz_dots<<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cB, ld);
+    SQ_LAUNCH_CHECK(h);
+    k_lz_update<<<eb, 256, 0, s>>>(g, w, V, i + 1, vstride, cB, ld, W);
+    SQ_LAUNCH_CHECK(h);
+    k_lz_dots<<<dim3(1, nst), kThreads, 0, s>>>(g, w, W, 1, vstride, W, nrm, ld);
+    SQ_LAUNCH_CHECK(h);
+    k_lz_step<<<cb, 128, 0, s>>>(ncols, i, kk, k, cA, cB, ld, nrm, alpha, beta, keff);
+    SQ_LAUNCH_CHECK(h);
+    if (i < kk - 1) {
+      k_lz_scale<<<eb, 256, 0, s>>>(g, w, W, nrm, ld, keff, V + (size_t)(i + 1) * vstride, 0);
+      SQ_LAUNCH_CHECK(h);
+    }
+  }
+  k_lz_bounds<<<1, 256, 0, s>>>(ncols, k, alpha, beta, keff, h->d.scal);
+  SQ_LAUNCH_CHECK(h);
+  double b2[2];
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(b2, h->d.scal + 8, sizeof(b2), cudaMemcpyDeviceToHost, s));
+  SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (!(b2[0] < b2[1]) || !std::isfinite(b2[0]) || !std::isfinite(b2[1]))
+    return fail(h, SQ_ERR_CUDA, "Lanczos bounds are not finite");
+  return set_bounds(h, b2[0], b2[1]);
+}
+
+}  // namespace sq

@@ -1,0 +1,218 @@
+// Fermi level and contraction kernels (FP64).
+//
+//   R^j      = sum_q rho_q^j                                    (node sums, fixed order)
+//   F_k      = sum'_j cos(j theta_k) R^j,  theta_k = pi (k + 1/2) / M
+//   N(mu)    = 2 sum'_j c^j(mu) R^j = (4/M) sum_k g((chi + zeta cos theta_k - mu)/kT) F_k
+// because c^j = (2/M) sum_k g(cos theta_k) cos(j theta_k) is the M-point Chebyshev-Gauss
+// rule for the Clenshaw-Curtis coefficient integral of Sec. 4; bisection on N(mu) = N_e.
+// The contraction evaluates c^j, d^j (coefficients of r g(r), App. A) and s^j (entropy
+// function) at mu and forms rho_q, E_band, E_s, E_nl and sigma (Sec. 4 stress sums).
+#include "sq_device.cuh"
+
+namespace sq {
+
+__device__ __forceinline__ double fermi_d(double x) {
+  const double ex = exp(-fabs(x));
+  return (x > 0.0) ? ex / (1.0 + ex) : 1.0 / (1.0 + ex);
+}
+
+// g ln g + (1 - g) ln(1 - g) at g = fermi(x), stable form -[ln(1+e^-|x|) + |x| e^-|x|/(1+e^-|x|)]
+__device__ __forceinline__ double entropy_d(double x) {
+  const double ax = fabs(x), ex = exp(-ax);
+  return -(log1p(ex) + ax * ex / (1.0 + ex));
+}
+
+// Deterministic block sum (blockDim.x = 256 or 1024, power of two).
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_rsum(const double* __restrict__ mom, int Nd, int n_pl, double* __restrict__ R) {
+  __shared__ double sh[256];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < Nd; q += blockDim.x) s += mom[((size_t)q * (n_pl + 1) + j) * SQ_N_MOMENTS];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) R[j] = s;
+}
+
+__global__ void k_cosF(const double* __restrict__ R, int n_pl, int M, double* __restrict__ F) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const double th = M_PI * (k + 0.5) / M;
+  double s = 0.5 * R[0];
+  for (int j = 1; j <= n_pl; ++j) s += cos(j * th) * R[j];
+  F[k] = s;
+}
+
+__device__ double count_at(const double* F, int M, double chi_q, double zeta_q, double kT, double mu, double* sh) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const double r = cos(M_PI * (k + 0.5) / M);
+    s += fermi_d((chi_q + zeta_q * r - mu) / kT) * F[k];
+  }
+  return 4.0 / M * block_sum(s, sh);
+}
+
+// Single block. scal[0], scal[1]: bounds; writes scal[2] = mu, status[kStNoBracket].
+__global__ void k_bisect(const double* __restrict__ F, int M, double kT, double n_e, double* __restrict__ scal,
+                         int* __restrict__ status) {
+  __shared__ double sh[1024];
+  const double lam_lo = scal[0], lam_hi = scal[1];
+  const double chi_q = 0.5 * (lam_hi + lam_lo), zeta_q = 0.5 * (lam_hi - lam_lo);
+  double lo = lam_lo - 40.0 * kT, hi = lam_hi + 40.0 * kT;
+  const double nlo = count_at(F, M, chi_q, zeta_q, kT, lo, sh);
+  const double nhi = count_at(F, M, chi_q, zeta_q, kT, hi, sh);
+  if (!(nlo < n_e && n_e < nhi)) {
+    if (threadIdx.x == 0) {
+      status[kStNoBracket] = 1;
+      scal[2] = NAN;
+    }
+    return;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_at(F, M, chi_q, zeta_q, kT, mid, sh) < n_e) lo = mid;
+    else hi = mid;
+    if (hi - lo < 1e-13 * fmax(1.0, fabs(mid))) break;
+  }
+  if (threadIdx.x == 0) {
+    scal[2] = 0.5 * (lo + hi);
+    status[kStNoBracket] = 0;
+  }
+}
+
+// Coefficients at mu = scal[3]: block 0 -> c, 1 -> d (r g(r)), 2 -> s (entropy function).
+__global__ void k_coef(const double* __restrict__ scal, double kT, int n_pl, int M, double* __restrict__ coef) {
+  extern __shared__ double fv[];
+  const double lam_lo = scal[0], lam_hi = scal[1], mu = scal[3];
+  const double chi_q = 0.5 * (lam_hi + lam_lo), zeta_q = 0.5 * (lam_hi - lam_lo);
+  const int which = blockIdx.x;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const double r = cos(M_PI * (k + 0.5) / M);
+    const double x = (chi_q + zeta_q * r - mu) / kT;
+    fv[k] = (which == 0) ? fermi_d(x) : (which == 1) ? r * fermi_d(x) : entropy_d(x);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j <= n_pl; j += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < M; ++k) s += fv[k] * cos(j * (M_PI * (k + 0.5) / M));
+    coef[which * (n_pl + 1) + j] = 2.0 / M * s;
+  }
+}
+
+constexpr int kNPart = 19;
+
+__global__ void k_contract(const double* __restrict__ mom, const double* __restrict__ coef,
+                           const double* __restrict__ scal, int Nd, int n_pl, double dV, double* __restrict__ rho,
+                           double* __restrict__ part) {
+  __shared__ double sh[256];
+  const double lam_lo = scal[0], lam_hi = scal[1];
+  const double chi_q = 0.5 * (lam_hi + lam_lo), zeta_q = 0.5 * (lam_hi - lam_lo);
+  const double* c = coef;
+  const double* d = coef + (n_pl + 1);
+  const double* s = coef + 2 * (n_pl + 1);
+  double acc[kNPart];
+  for (int k = 0; k < kNPart; ++k) acc[k] = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Nd; q += gridDim.x * blockDim.x) {
+    double r = 0.0;
+    double loc[kNPart];
+    for (int k = 0; k < kNPart; ++k) loc[k] = 0.0;
+    for (int j = 0; j <= n_pl; ++j) {
+      const double wp = (j == 0) ? 0.5 : 1.0;
+      const double* m = mom + ((size_t)q * (n_pl + 1) + j) * SQ_N_MOMENTS;
+      const double cj = wp * c[j];
+      r += cj * m[0];
+      loc[0] += wp * (chi_q * c[j] + zeta_q * d[j]) * m[0];
+      loc[1] += wp * s[j] * m[0];
+      loc[2] += cj * m[7];
+      for (int k = 0; k < 6; ++k) loc[3 + k] += cj * m[1 + k];
+      for (int k = 0; k < 9; ++k) loc[9 + k] += cj * m[8 + k];
+    }
+    rho[q] = 2.0 / dV * r;
+    loc[18] = r;
+    for (int k = 0; k < kNPart; ++k) acc[k] += loc[k];
+  }
+  for (int k = 0; k < kNPart; ++k) {
+    const double v = block_sum(acc[k], sh);
+    if (threadIdx.x == 0) part[blockIdx.x * kNPart + k] = v;
+  }
+}
+
+// out (scal + 16): [E_band, E_s, E_nl, N_check, sigma(9, row-major)]
+__global__ void k_contract_final(const double* __restrict__ part, int nblk, double kT, double vol,
+                                 double* __restrict__ scal) {
+  if (threadIdx.x != 0) return;
+  double tot[kNPart];
+  for (int k = 0; k < kNPart; ++k) tot[k] = 0.0;
+  for (int b = 0; b < nblk; ++b)
+    for (int k = 0; k < kNPart; ++k) tot[k] += part[b * kNPart + k];
+  double* out = scal + 16;
+  out[0] = 2.0 * tot[0];
+  out[1] = 2.0 * kT * tot[1];
+  const double E_nl = 2.0 * tot[2];
+  out[2] = E_nl;
+  out[3] = 2.0 * tot[18];   // |dOmega| sum_q rho_q = 2 sum_q sum' c rho^j
+  const int ka[6] = {0, 1, 2, 1, 0, 0}, kb[6] = {0, 1, 2, 2, 2, 1};
+  double sig[9];
+  for (int k = 0; k < 9; ++k) sig[k] = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    sig[3 * ka[k] + kb[k]] += 2.0 * tot[3 + k];
+    if (ka[k] != kb[k]) sig[3 * kb[k] + ka[k]] += 2.0 * tot[3 + k];
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      sig[3 * a + b] += -2.0 * ((a == b ? 0.5 * E_nl : 0.0) + 2.0 * tot[9 + 3 * a + b]);
+  for (int k = 0; k < 9; ++k) out[4 + k] = sig[k] / vol;
+}
+
+__global__ void k_set_scalar(double* __restrict__ scal, int idx, double v) { scal[idx] = v; }
+
+int run_fermi(sq_handle* h, double* mu_out) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  k_rsum<<<g.n_pl + 1, 256, 0, s>>>(h->d.mom, h->Nd, g.n_pl, h->d.R);
+  SQ_LAUNCH_CHECK(h);
+  k_cosF<<<(h->M + 255) / 256, 256, 0, s>>>(h->d.R, g.n_pl, h->M, h->d.cosF);
+  SQ_LAUNCH_CHECK(h);
+  k_bisect<<<1, 1024, 0, s>>>(h->d.cosF, h->M, h->kT, h->n_e, h->d.scal, h->d.status);
+  SQ_LAUNCH_CHECK(h);
+  double mu = 0.0;
+  int st[kStCount];
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(&mu, h->d.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(st, h->d.status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (st[kStNoBracket]) return fail(h, SQ_ERR_NO_BRACKET, "N(mu) - N_e has no sign change on the bisection bracket");
+  if (mu_out) *mu_out = mu;
+  return SQ_OK;
+}
+
+int run_contraction(sq_handle* h, double mu, double* rho_dev, double* out_host) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  k_set_scalar<<<1, 1, 0, s>>>(h->d.scal, 3, mu);
+  SQ_LAUNCH_CHECK(h);
+  k_coef<<<3, 256, sizeof(double) * h->M, s>>>(h->d.scal, h->kT, g.n_pl, h->M, h->d.coef);
+  SQ_LAUNCH_CHECK(h);
+  const int nblk = std::min(1024, (h->Nd + 255) / 256);
+  k_contract<<<nblk, 256, 0, s>>>(h->d.mom, h->d.coef, h->d.scal, h->Nd, g.n_pl, g.dV, rho_dev, h->d.part);
+  SQ_LAUNCH_CHECK(h);
+  k_contract_final<<<1, 32, 0, s>>>(h->d.part, nblk, h->kT, h->vol, h->d.scal);
+  SQ_LAUNCH_CHECK(h);
+  if (out_host) {
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(out_host, h->d.scal + 16, 13 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
+  return SQ_OK;
+}
+
+
+}  // namespace sq

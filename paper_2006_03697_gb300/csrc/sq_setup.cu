@@ -1,0 +1,270 @@
+// Setup kernels: projector tables, per-tile atom-image lists, per-brick lists, the
+// projector weights at the nodes (A) and the per-node nonlocal-stress weights (W).
+//
+// Projectors (Sec. 2, E_nl and sigma^III; Gaussian stand-ins):
+//   chi_00 = (pi w^2)^(-3/4) exp(-r^2 / 2w^2),  chi_1m = sqrt(2)/w d_m (pi w^2)^(-3/4) exp(-r^2 / 2w^2)
+// sampled at the absolute lattice points x = u h of each atom's support box (base image).
+// A periodic image of the atom shifted by s cells uses the same table at u - s n.
+#include "sq_device.cuh"
+
+namespace sq {
+
+// chs layout per channel: [gamma*dV, l, m, width, rcut, 0]
+template <typename Real>
+__global__ void k_chi_tables(Geo g, const AtomTab* __restrict__ atoms, const double* __restrict__ chs,
+                             Real* __restrict__ chi) {
+  const AtomTab at = atoms[blockIdx.x];
+  const int boxpts = at.dim[0] * at.dim[1] * at.dim[2];
+  for (int i = threadIdx.x; i < boxpts; i += blockDim.x) {
+    const int lx = i % at.dim[0], ly = (i / at.dim[0]) % at.dim[1], lz = i / (at.dim[0] * at.dim[1]);
+    const double d[3] = {(at.lo[0] + lx) * g.h[0] - at.R[0], (at.lo[1] + ly) * g.h[1] - at.R[1],
+                         (at.lo[2] + lz) * g.h[2] - at.R[2]};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    for (int c = 0; c < at.nch; ++c) {
+      const double* sp = chs + 6 * (at.ch0 + c);
+      const int l = int(sp[1]), mch = int(sp[2]);
+      const double w = sp[3], rc = sp[4];
+      double val = 0.0;
+      if (r2 <= rc * rc) {
+        const double base = pow(M_PI * w * w, -0.75) * exp(-r2 / (2.0 * w * w));
+        val = (l == 0) ? base : sqrt(2.0) / w * d[mch] * base;
+      }
+      chi[at.off + (long long)c * boxpts + i] = Real(val);
+    }
+  }
+}
+
+// One block per tile of the wave: list the atom images (atom, shift s) whose support box
+// meets the tile's union window, atom-major then s (x fastest); assign projector rows.
+__global__ void k_tile_entries(Geo g, Wave w, const AtomTab* __restrict__ atoms, TileEntry* __restrict__ entries,
+                               int* __restrict__ n_entries, int* __restrict__ n_rows, int* __restrict__ status) {
+  const int tl = blockIdx.x, t = wave_tile(w, tl);
+  int o[3];
+  tile_origin(g, t, o);
+  int ulo[3], uhi[3];
+  for (int a = 0; a < 3; ++a) {
+    ulo[a] = o[a] - g.m[a];
+    uhi[a] = ulo[a] + g.U[a] - 1;
+  }
+  TileEntry* out = entries + (size_t)tl * g.e_cap;
+  int base_e = 0, base_r = 0;
+  for (int a0 = 0; a0 < g.n_atoms; a0 += blockDim.x) {
+    const int J = a0 + threadIdx.x;
+    int cnt = 0, nch = 0, slo[3] = {0, 0, 0}, ns[3] = {0, 0, 0};
+    if (J < g.n_atoms) {
+      const AtomTab at = atoms[J];
+      nch = at.nch;
+      if (nch > 0 && at.dim[0] > 0 && at.dim[1] > 0 && at.dim[2] > 0) {
+        cnt = 1;
+        for (int a = 0; a < 3; ++a) {
+          slo[a] = ceil_div_d(ulo[a] - (at.lo[a] + at.dim[a] - 1), g.n[a]);
+          const int shi = floor_div_d(uhi[a] - at.lo[a], g.n[a]);
+          ns[a] = max(0, shi - slo[a] + 1);
+          cnt *= ns[a];
+        }
+      }
+    }
+    int tot_e, tot_r;
+    const int off_e = block_exclusive_scan(cnt, &tot_e);
+    const int off_r = block_exclusive_scan(cnt * nch, &tot_r);
+    for (int k = 0; k < cnt; ++k) {
+      const int idx = base_e + off_e + k;
+      if (idx < g.e_cap && base_r + off_r + (k + 1) * nch <= g.r_cap) {
+        TileEntry e;
+        e.atom = J;
+        e.s[0] = slo[0] + k % ns[0];
+        e.s[1] = slo[1] + (k / ns[0]) % ns[1];
+        e.s[2] = slo[2] + k / (ns[0] * ns[1]);
+        e.row0 = base_r + off_r + k * nch;
+        e.pad = 0;
+        out[idx] = e;
+      }
+    }
+    base_e += tot_e;
+    base_r += tot_r;
+  }
+  if (threadIdx.x == 0) {
+    const bool over = base_e > g.e_cap || base_r > g.r_cap;
+    // on overflow nothing downstream may index past the capacities: empty lists, error flag
+    n_entries[tl] = over ? 0 : base_e;
+    n_rows[tl] = over ? 0 : base_r;
+    if (over) atomicOr(status + kStOverflow, 1);
+  }
+}
+
+// One warp per (brick, tile): entries whose support box meets the brick, in entry order.
+__global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const TileEntry* __restrict__ entries,
+                              const int* __restrict__ n_entries, int* __restrict__ blist, int* __restrict__ bn,
+                              int* __restrict__ status) {
+  const int br = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl), lane = threadIdx.x;
+  int o[3];
+  tile_origin(g, t, o);
+  const int bx = br % g.nbr[0], by = (br / g.nbr[0]) % g.nbr[1], bz = br / (g.nbr[0] * g.nbr[1]);
+  const int bl[3] = {o[0] - g.m[0] + bx * kBrick, o[1] - g.m[1] + by * kBrick, o[2] - g.m[2] + bz * kBrick};
+  const int bhi[3] = {o[0] - g.m[0] + min(g.U[0], (bx + 1) * kBrick) - 1,
+                      o[1] - g.m[1] + min(g.U[1], (by + 1) * kBrick) - 1,
+                      o[2] - g.m[2] + min(g.U[2], (bz + 1) * kBrick) - 1};
+  const int ne = n_entries[tl];
+  const TileEntry* ent = entries + (size_t)tl * g.e_cap;
+  int* out = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
+  int cnt = 0;
+  for (int e0 = 0; e0 < ne; e0 += 32) {
+    const int e = e0 + lane;
+    bool hit = false;
+    if (e < ne) {
+      const TileEntry te = ent[e];
+      const AtomTab at = atoms[te.atom];
+      hit = true;
+      for (int a = 0; a < 3; ++a) {
+        const int lo = at.lo[a] + te.s[a] * g.n[a], hi = lo + at.dim[a] - 1;
+        hit = hit && (lo <= bhi[a]) && (hi >= bl[a]);
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+    if (hit && pos < g.br_cap) out[pos] = e;
+    cnt += __popc(mask);
+  }
+  if (lane == 0) {
+    bn[(size_t)tl * g.nbricks + br] = min(cnt, g.br_cap);
+    if (cnt > g.br_cap) atomicOr(status + kStOverflow, 2);
+  }
+}
+
+// A[row][q] = gamma_row |dOmega| chi_row(x_q): the coefficients of w_q^T V_nl,q.
+template <typename Real>
+__global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ chs,
+                         const Real* __restrict__ chi, const TileEntry* __restrict__ entries,
+                         const int* __restrict__ n_entries, Real* __restrict__ A) {
+  const int tl = blockIdx.x, t = wave_tile(w, tl);
+  int o[3];
+  tile_origin(g, t, o);
+  const int ne = n_entries[tl];
+  const TileEntry* ent = entries + (size_t)tl * g.e_cap;
+  Real* At = A + (size_t)tl * g.r_cap * g.B;
+  for (int i = threadIdx.x; i < ne * g.B; i += blockDim.x) {
+    const int e = i / g.B, q = i % g.B;
+    const TileEntry te = ent[e];
+    const AtomTab at = atoms[te.atom];
+    int qo[3];
+    node_offset(g, q, qo);
+    const bool valid = node_valid(g, o, qo);
+    const int li = valid ? box_index(at, te.s, g.n, o[0] + qo[0], o[1] + qo[1], o[2] + qo[2]) : -1;
+    const int boxpts = at.dim[0] * at.dim[1] * at.dim[2];
+    for (int c = 0; c < at.nch; ++c) {
+      const double v = (li >= 0) ? chs[6 * (at.ch0 + c)] * double(chi[at.off + (long long)c * boxpts + li]) : 0.0;
+      At[(size_t)(te.row0 + c) * g.B + q] = Real(v);
+    }
+  }
+}
+
+// W_b(u, q) = sum_rows A[row][q] chi_row(u) (x_u,b - R_b) on the window of q (zero outside):
+// contracting the atom sum of the sigma^III term once, S^j_ab = sum_u W_b(u,q) (grad_a t^j)(u).
+template <typename Real>
+__global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const Real* __restrict__ chi,
+                         const TileEntry* __restrict__ entries, const int* __restrict__ blist,
+                         const int* __restrict__ bn, const Real* __restrict__ A, Real* __restrict__ W) {
+  const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
+  int o[3];
+  tile_origin(g, t, o);
+  const int z0 = slab * kBrick, nz = min(kBrick, g.U[2] - z0);
+  const int nel = g.U[0] * g.U[1] * nz * g.B;
+  const TileEntry* ent = entries + (size_t)tl * g.e_cap;
+  const Real* At = A + (size_t)tl * g.r_cap * g.B;
+  Real* Wt = W + (size_t)tl * 3 * g.Upts * g.B;
+  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+    const int q = i % g.B, p = i / g.B;
+    const int ux = p % g.U[0], uy = (p / g.U[0]) % g.U[1], uz = z0 + p / (g.U[0] * g.U[1]);
+    const int pt = (uz * g.U[1] + uy) * g.U[0] + ux;
+    int qo[3];
+    node_offset(g, q, qo);
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (node_valid(g, o, qo) && in_window(g, qo, ux, uy, uz)) {
+      const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
+      const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
+      const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
+      const int nb = bn[(size_t)tl * g.nbricks + br];
+      const double x[3] = {ax * g.h[0], ay * g.h[1], az * g.h[2]};
+      for (int k = 0; k < nb; ++k) {
+        const TileEntry te = ent[lst[k]];
+        const AtomTab at = atoms[te.atom];
+        const int li = box_index(at, te.s, g.n, ax, ay, az);
+        if (li < 0) continue;
+        const int boxpts = at.dim[0] * at.dim[1] * at.dim[2];
+        double cs = 0.0;
+        for (int c = 0; c < at.nch; ++c)
+          cs += double(At[(size_t)(te.row0 + c) * g.B + q]) * double(chi[at.off + (long long)c * boxpts + li]);
+        if (cs == 0.0) continue;
+        for (int b = 0; b < 3; ++b) acc[b] += cs * (x[b] - (at.R[b] + te.s[b] * g.L[b]));
+      }
+    }
+    for (int b = 0; b < 3; ++b) Wt[((size_t)b * g.Upts + pt) * g.B + q] = Real(acc[b]);
+  }
+}
+
+// t^0 = w_q: one at the node's own point, zero elsewhere (and zero columns for padding nodes).
+template <typename Real>
+__global__ void k_init_t0(Geo g, Wave w, Real* __restrict__ T0) {
+  const size_t per_tile = (size_t)g.Upts * g.B;
+  const size_t total = per_tile * w.ntiles;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int tl = int(i / per_tile);
+    const int r = int(i % per_tile);
+    const int q = r % g.B, pt = r / g.B;
+    int o[3], qo[3];
+    tile_origin(g, wave_tile(w, tl), o);
+    node_offset(g, q, qo);
+    const int cpt = ((qo[2] + g.m[2]) * g.U[1] + (qo[1] + g.m[1])) * g.U[0] + (qo[0] + g.m[0]);
+    T0[i] = (node_valid(g, o, qo) && pt == cpt) ? Real(1) : Real(0);
+  }
+}
+
+template <typename Real>
+static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, Real* A, Real* W, Real* T0) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows,
+                                          h->d.status);
+  SQ_LAUNCH_CHECK(h);
+  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries,
+                                                          h->wb.brick_list, h->wb.brick_n, h->d.status);
+  SQ_LAUNCH_CHECK(h);
+  k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A);
+  SQ_LAUNCH_CHECK(h);
+  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 256, 0, s>>>(g, w, h->d.atoms, chi, h->wb.entries, h->wb.brick_list,
+                                                          h->wb.brick_n, A, W);
+  SQ_LAUNCH_CHECK(h);
+  k_init_t0<Real><<<1024, 256, 0, s>>>(g, w, T0);
+  SQ_LAUNCH_CHECK(h);
+  return SQ_OK;
+}
+
+int build_wave_entries(sq_handle* h, const Wave& w) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows, h->d.status);
+  SQ_LAUNCH_CHECK(h);
+  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries,
+                                                          h->wb.brick_list, h->wb.brick_n, h->d.status);
+  SQ_LAUNCH_CHECK(h);
+  return SQ_OK;
+}
+
+int build_tables(sq_handle* h) {
+  if (h->geo.n_atoms == 0 || h->table_len == 0) return SQ_OK;
+  k_chi_tables<double><<<h->geo.n_atoms, 256, 0, h->stream>>>(h->geo, h->d.atoms, h->d.gdv, h->d.chi64);
+  SQ_LAUNCH_CHECK(h);
+  if (h->precision == SQ_MIXED) {
+    k_chi_tables<float><<<h->geo.n_atoms, 256, 0, h->stream>>>(h->geo, h->d.atoms, h->d.gdv, h->d.chi32);
+    SQ_LAUNCH_CHECK(h);
+  }
+  return SQ_OK;
+}
+
+int build_wave_lists(sq_handle* h, const Wave& w) {
+  if (h->precision == SQ_FP64)
+    return wave_lists_t<double>(h, w, h->d.chi64, (double*)h->wb.A, (double*)h->wb.W, (double*)h->wb.T[0]);
+  return wave_lists_t<float>(h, w, h->d.chi32, (float*)h->wb.A, (float*)h->wb.W, (float*)h->wb.T[0]);
+}
+
+}  // namespace sq

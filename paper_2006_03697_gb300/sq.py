@@ -1,0 +1,245 @@
+"""Thin ctypes binding of the C ABI in include/sq_api.h (argument marshalling only).
+
+Every function keeps the C name and returns what the C call writes; a non-zero status
+raises SQError with the library's error text. The CUDA library must have been built
+(paper_2006_03697_gb300.build); there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libsq_gb300.so"
+
+SQ_OK = 0
+SQ_ERR_INVALID_ARG = 1
+SQ_ERR_OOM = 2
+SQ_ERR_CUDA = 3
+SQ_ERR_NO_BRACKET = 4
+SQ_ERR_TIMEOUT = 5
+SQ_ERR_STATE = 6
+SQ_FP64 = 0
+SQ_MIXED = 1
+SQ_BOUNDS_LANCZOS = 0
+SQ_BOUNDS_GIVEN = 1
+SQ_N_MOMENTS = 17
+
+EXPORTED = [
+    "sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
+    "sq_density_energy_stress_dev", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
+    "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_destroy", "sq_last_error",
+]
+SQ_K_STENCIL = 0
+SQ_K_PROJECT = 1
+SQ_K_MOMENTS = 2
+
+
+class sq_proj(C.Structure):
+    _fields_ = [("l", C.c_int), ("width", C.c_double), ("gamma", C.c_double), ("rcut", C.c_double)]
+
+
+class sq_instance_desc(C.Structure):
+    _fields_ = [
+        ("L", C.c_double * 3), ("n", C.c_int * 3), ("n_o", C.c_int),
+        ("v_eff", C.POINTER(C.c_double)),
+        ("n_atoms", C.c_int), ("pos", C.POINTER(C.c_double)), ("species", C.POINTER(C.c_int)),
+        ("n_species", C.c_int), ("proj_offset", C.POINTER(C.c_int)), ("proj", C.POINTER(sq_proj)),
+        ("kT", C.c_double), ("n_e", C.c_double), ("r_cut", C.c_double), ("n_pl", C.c_int),
+        ("precision", C.c_int), ("bounds_mode", C.c_int),
+        ("lambda_lo", C.c_double), ("lambda_hi", C.c_double),
+        ("cheb_quad_M", C.c_int), ("lanczos_k", C.c_int), ("stream", C.c_void_p),
+    ]
+
+
+class sq_energies(C.Structure):
+    _fields_ = [("E_band", C.c_double), ("E_s", C.c_double), ("E_nl", C.c_double),
+                ("F", C.c_double), ("N_check", C.c_double), ("mu", C.c_double)]
+
+
+class SQError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Loads the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2006_03697_gb300.build")
+        L = C.CDLL(str(LIB_PATH))
+        H = C.c_void_p
+        L.sq_setup.argtypes = [C.POINTER(sq_instance_desc), C.POINTER(H)]
+        L.sq_moments.argtypes = [H]
+        L.sq_fermi_level.argtypes = [H, C.POINTER(C.c_double)]
+        L.sq_density_energy_stress.argtypes = [H, C.c_double, C.c_void_p, C.POINTER(sq_energies), C.c_void_p]
+        L.sq_density_energy_stress_dev.argtypes = [H, C.c_double, C.c_void_p, C.POINTER(sq_energies), C.c_void_p]
+        L.sq_get_bounds.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.sq_moments_copy.argtypes = [H, C.c_void_p]
+        L.sq_footprint_bytes.argtypes = [C.POINTER(sq_instance_desc)]
+        L.sq_footprint_bytes.restype = C.c_size_t
+        L.sq_kernel_launches.argtypes = [H]
+        L.sq_kernel_launches.restype = C.c_longlong
+        L.sq_kernel_timing.argtypes = [H, C.c_int]
+        L.sq_kernel_timing.restype = C.c_int
+        L.sq_kernel_timing_read.argtypes = [H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
+        L.sq_kernel_timing_read.restype = C.c_int
+        L.sq_destroy.argtypes = [H]
+        L.sq_destroy.restype = None
+        L.sq_last_error.argtypes = [H]
+        L.sq_last_error.restype = C.c_char_p
+        for name in ("sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
+                     "sq_density_energy_stress_dev", "sq_get_bounds", "sq_moments_copy"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class Desc:
+    """Owns the host arrays a sq_instance_desc points to (built from a workloads dict)."""
+
+    def __init__(self, inst: dict, precision=SQ_FP64, bounds=None, stream=None, lanczos_k=0):
+        self.v = np.ascontiguousarray(inst["v_eff"], dtype=np.float64)
+        self.pos = np.ascontiguousarray(np.asarray(inst["pos"], dtype=np.float64).reshape(-1, 3))
+        self.species = np.ascontiguousarray(inst["species"], dtype=np.int32)
+        offs = [0]
+        plist = []
+        for sp in inst["proj"]:
+            for pj in sp:
+                plist.append(sq_proj(int(pj["l"]), float(pj["width"]), float(pj["gamma"]),
+                                     float(pj.get("rcut", 0.0) or 0.0)))
+            offs.append(len(plist))
+        self.offs = np.ascontiguousarray(offs, dtype=np.int32)
+        self.proj = (sq_proj * max(1, len(plist)))(*plist)
+        d = sq_instance_desc()
+        for a in range(3):
+            d.L[a] = float(inst["L"][a])
+            d.n[a] = int(inst["n"][a])
+        d.n_o = int(inst["n_o"])
+        d.v_eff = self.v.ctypes.data_as(C.POINTER(C.c_double))
+        d.n_atoms = int(self.pos.shape[0])
+        d.pos = self.pos.ctypes.data_as(C.POINTER(C.c_double))
+        d.species = self.species.ctypes.data_as(C.POINTER(C.c_int))
+        d.n_species = len(inst["proj"])
+        d.proj_offset = self.offs.ctypes.data_as(C.POINTER(C.c_int))
+        d.proj = C.cast(self.proj, C.POINTER(sq_proj))
+        d.kT = float(inst["kT"])
+        d.n_e = float(inst["n_e"])
+        d.r_cut = float(inst["r_cut"])
+        d.n_pl = int(inst["n_pl"])
+        d.precision = int(precision)
+        if bounds is None:
+            d.bounds_mode = SQ_BOUNDS_LANCZOS
+        else:
+            d.bounds_mode = SQ_BOUNDS_GIVEN
+            d.lambda_lo, d.lambda_hi = float(bounds[0]), float(bounds[1])
+        d.cheb_quad_M = int(inst.get("M", 2048))
+        d.lanczos_k = int(lanczos_k)
+        d.stream = stream
+        self.c = d
+
+
+def _check(rc, h=None):
+    if rc != SQ_OK:
+        msg = lib().sq_last_error(h).decode(errors="replace")
+        raise SQError(rc, msg)
+
+
+def sq_setup(desc: Desc):
+    h = C.c_void_p()
+    _check(lib().sq_setup(C.byref(desc.c), C.byref(h)), None)
+    return h
+
+
+def sq_moments(h):
+    _check(lib().sq_moments(h), h)
+
+
+def sq_fermi_level(h) -> float:
+    mu = C.c_double()
+    _check(lib().sq_fermi_level(h, C.byref(mu)), h)
+    return mu.value
+
+
+def sq_density_energy_stress(h, mu: float, nd: int | None = None):
+    """Host outputs: (rho (N_d,) or None, energies dict, sigma (3, 3))."""
+    e = sq_energies()
+    sig = np.zeros(9)
+    rho = np.zeros(nd) if nd else None
+    _check(lib().sq_density_energy_stress(h, C.c_double(mu), rho.ctypes.data if rho is not None else None,
+                                          C.byref(e), sig.ctypes.data), h)
+    en = {k: getattr(e, k) for k, _ in sq_energies._fields_}
+    return rho, en, sig.reshape(3, 3)
+
+
+def sq_density_energy_stress_dev(h, mu: float, rho_dev_ptr: int | None, sigma_dev_ptr: int | None, energies=True):
+    e = sq_energies()
+    _check(lib().sq_density_energy_stress_dev(h, C.c_double(mu), rho_dev_ptr, C.byref(e) if energies else None,
+                                              sigma_dev_ptr), h)
+    return {k: getattr(e, k) for k, _ in sq_energies._fields_} if energies else None
+
+
+def sq_get_bounds(h):
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib().sq_get_bounds(h, C.byref(lo), C.byref(hi)), h)
+    return lo.value, hi.value
+
+
+def sq_moments_copy(h, nd: int, n_pl: int):
+    out = np.zeros((nd, n_pl + 1, SQ_N_MOMENTS))
+    _check(lib().sq_moments_copy(h, out.ctypes.data), h)
+    return out
+
+
+def sq_footprint_bytes(desc: Desc) -> int:
+    return int(lib().sq_footprint_bytes(C.byref(desc.c)))
+
+
+def sq_kernel_launches(h) -> int:
+    return int(lib().sq_kernel_launches(h))
+
+
+def sq_kernel_timing(h, enable: bool):
+    _check(lib().sq_kernel_timing(h, 1 if enable else 0), h)
+
+
+def sq_kernel_timing_read(h, kid: int):
+    """(launches, total_ms, algorithmic_bytes) of kernel class kid since timing was enabled."""
+    n, ms, b = C.c_longlong(), C.c_double(), C.c_double()
+    _check(lib().sq_kernel_timing_read(h, kid, C.byref(n), C.byref(ms), C.byref(b)), h)
+    return n.value, ms.value, b.value
+
+
+def sq_destroy(h):
+    if h:
+        lib().sq_destroy(h)
+
+
+def sq_last_error(h=None) -> str:
+    return lib().sq_last_error(h).decode(errors="replace")
+
+
+def run(inst: dict, precision=SQ_FP64, bounds=None, want_moments=False, stream=None):
+    """setup -> moments -> Fermi level -> contraction -> destroy; returns a result dict."""
+    d = Desc(inst, precision, bounds, stream)
+    h = sq_setup(d)
+    try:
+        sq_moments(h)
+        mu = sq_fermi_level(h)
+        nd = int(np.prod(inst["n"]))
+        rho, en, sig = sq_density_energy_stress(h, mu, nd)
+        out = {"mu": mu, "rho": rho, "sigma": sig, "bounds": sq_get_bounds(h),
+               "launches": sq_kernel_launches(h)}
+        out.update(en)
+        if want_moments:
+            out["moments"] = sq_moments_copy(h, nd, int(inst["n_pl"]))
+        return out
+    finally:
+        sq_destroy(h)

@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads and exports every symbol include/sq_api.h declares;
+host-side validation and footprint logic (no GPU compute calls)."""
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from workloads import make_instance, tiny_instance
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def sq():
+    from paper_2006_03697_gb300 import build
+    build.build()
+    from paper_2006_03697_gb300 import sq as mod
+    return mod
+
+
+def test_header_symbols_exported(sq):
+    hdr = (ROOT / "include" / "sq_api.h").read_text()
+    names = set(re.findall(r"\b(sq_[a-z_]+)\s*\(", hdr))
+    assert names, "no declarations parsed"
+    L = sq.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert names == set(sq.EXPORTED)
+
+
+def test_footprint_scales_with_problem(sq):
+    f1 = sq.sq_footprint_bytes(sq.Desc(make_instance(1), sq.SQ_FP64, bounds=(-1.0, 40.0)))
+    f2 = sq.sq_footprint_bytes(sq.Desc(make_instance(2), sq.SQ_FP64, bounds=(-1.0, 130.0)))
+    f2m = sq.sq_footprint_bytes(sq.Desc(make_instance(2), sq.SQ_MIXED, bounds=(-1.0, 130.0)))
+    assert 0 < f1 < f2
+    assert 0 < f2m <= f2
+    assert f2 < 64 << 30
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n_o", 0), ("n_o", 7), ("kT", 0.0), ("n_e", 0.0), ("n_e", 1e9), ("r_cut", 0.01), ("n_pl", 0),
+    ("precision", 5), ("bounds_mode", 9),
+])
+def test_setup_rejects_invalid_descriptor(sq, field, value):
+    d = sq.Desc(tiny_instance(seed=0), sq.SQ_FP64, bounds=(-1.0, 20.0))
+    setattr(d.c, field, value)
+    with pytest.raises(sq.SQError) as ei:
+        sq.sq_setup(d)
+    assert ei.value.code == sq.SQ_ERR_INVALID_ARG
+    assert sq.sq_last_error(None) != "no error"
+
+
+def test_setup_rejects_nan_potential_and_bad_bounds(sq):
+    inst = tiny_instance(seed=0)
+    inst["v_eff"] = np.asarray(inst["v_eff"]).copy()
+    inst["v_eff"][3] = np.nan
+    with pytest.raises(sq.SQError) as ei:
+        sq.sq_setup(sq.Desc(inst, sq.SQ_FP64, bounds=(-1.0, 20.0)))
+    assert ei.value.code == sq.SQ_ERR_INVALID_ARG
+    with pytest.raises(sq.SQError) as ei:
+        sq.sq_setup(sq.Desc(tiny_instance(seed=0), sq.SQ_FP64, bounds=(5.0, 5.0)))
+    assert ei.value.code == sq.SQ_ERR_INVALID_ARG
+
+
+def test_null_handle_calls_are_rejected(sq):
+    L = sq.lib()
+    assert L.sq_moments(None) == sq.SQ_ERR_INVALID_ARG
+    assert L.sq_fermi_level(None, None) == sq.SQ_ERR_INVALID_ARG
+    assert L.sq_kernel_launches(None) == 0
+    L.sq_destroy(None)
