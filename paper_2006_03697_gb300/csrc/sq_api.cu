@@ -97,6 +97,7 @@ struct Plan {
   std::vector<sq::AtomTab> atoms;
   std::vector<int> ch_l, ch_m;
   std::vector<double> ch_w, ch_rc, ch_gdv;
+  std::vector<double> rcmax;
   long long table_len = 0;
   int wave_cap = 0;
   std::vector<int> lz_tiles;    // sample tiles of the Lanczos bounds
@@ -118,6 +119,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
     g.h[a] = d->L[a] / d->n[a];
     g.m[a] = int(std::floor(d->r_cut / g.h[a] + 1e-9));
     g.U[a] = 2 * g.m[a] + g.b;
+    if (a == 0) g.U[a] = (g.U[a] + 3) / 4 * 4;   // x extent padded to whole 4-point bricks
     g.nbr[a] = (g.U[a] + sq::kBrick - 1) / sq::kBrick;
     g.tiles[a] = (g.n[a] + g.b - 1) / g.b;
   }
@@ -187,8 +189,10 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
       boxpts *= at.dim[a];
     }
     if (at.nch == 0) boxpts = 0;
+    P.rcmax.push_back(rc_max);
+    at.nchp = (at.nch + 3) / 4 * 4;
     at.off = off;
-    off += boxpts * at.nch;
+    off += boxpts * at.nchp;
     // capacity bounds: images of this atom that can meet a window of extent W on axis a
     long long nimg_u = 1, nimg_b = 1;
     for (int a = 0; a < 3; ++a) {
@@ -214,7 +218,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
                      size_t(g.nbricks) * (size_t(g.br_cap) + 1) * sizeof(int) +
                      3 * size_t(g.Upts) * tileB * real +        // T ring
                      3 * size_t(g.Upts) * tileB * real +        // W
-                     2 * size_t(g.r_cap) * tileB * real +       // A, P
+                     4 * size_t(g.r_cap) * tileB * real +       // A, P, Pg ping-pong
                      size_t(g.nslab) * tileB * 9 * sizeof(double);
   long long Nd = (long long)g.n[0] * g.n[1] * g.n[2];
   int M = d->cheb_quad_M > 0 ? d->cheb_quad_M : 2048;
@@ -409,6 +413,9 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->d.v32, sizeof(float) * Nd);
   SQ_ALLOC(h->d.atoms, sizeof(sq::AtomTab) * std::max<size_t>(1, P.atoms.size()));
   SQ_ALLOC(h->d.gdv, sizeof(double) * std::max(1, h->n_ch_total) * 6);
+  SQ_ALLOC(h->d.gdv64, sizeof(double) * std::max(1, h->n_ch_total));
+  SQ_ALLOC(h->d.rcmax, sizeof(double) * std::max<size_t>(1, P.rcmax.size()));
+  SQ_ALLOC(h->d.gdv32, sizeof(float) * std::max(1, h->n_ch_total));
   SQ_ALLOC(h->d.chi64, sizeof(double) * std::max<long long>(1, P.table_len));
   if (!f64) SQ_ALLOC(h->d.chi32, sizeof(float) * std::max<long long>(1, P.table_len));
   SQ_ALLOC(h->d.mom, sizeof(double) * size_t(Nd) * size_t(g.n_pl + 1) * SQ_N_MOMENTS);
@@ -429,6 +436,8 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->wb.W, real * size_t(wt) * 3 * g.Upts * g.B);
   SQ_ALLOC(h->wb.A, real * size_t(wt) * g.r_cap * g.B);
   SQ_ALLOC(h->wb.P, real * size_t(wt) * g.r_cap * g.B);
+  SQ_ALLOC(h->wb.Pg[0], real * size_t(wt) * g.r_cap * g.B);
+  SQ_ALLOC(h->wb.Pg[1], real * size_t(wt) * g.r_cap * g.B);
   SQ_ALLOC(h->wb.Spart, sizeof(double) * size_t(wt) * g.nslab * g.B * 9);
   if (!h->lanczos_tiles.empty()) {
     const size_t nst = h->lanczos_tiles.size();
@@ -465,6 +474,15 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_H2D(h->d.v32, v32.data(), sizeof(float) * Nd);
   if (!P.atoms.empty()) SQ_H2D(h->d.atoms, P.atoms.data(), sizeof(sq::AtomTab) * P.atoms.size());
   SQ_H2D(h->d.gdv, chs.data(), sizeof(double) * chs.size());
+  std::vector<double> g64(std::max(1, h->n_ch_total), 0.0);
+  std::vector<float> g32(std::max(1, h->n_ch_total), 0.f);
+  for (int c = 0; c < h->n_ch_total; ++c) {
+    g64[c] = P.ch_gdv[c];
+    g32[c] = float(P.ch_gdv[c]);
+  }
+  SQ_H2D(h->d.gdv64, g64.data(), sizeof(double) * g64.size());
+  if (!P.rcmax.empty()) SQ_H2D(h->d.rcmax, P.rcmax.data(), sizeof(double) * P.rcmax.size());
+  SQ_H2D(h->d.gdv32, g32.data(), sizeof(float) * g32.size());
   if (!h->lanczos_tiles.empty())
     SQ_H2D(h->d.lz_tiles, h->lanczos_tiles.data(), sizeof(int) * h->lanczos_tiles.size());
   double sc[64];

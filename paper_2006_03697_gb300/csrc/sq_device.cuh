@@ -47,6 +47,12 @@ __device__ __forceinline__ int box_index(const AtomTab& at, const int s[3], cons
   return (lz * at.dim[1] + ly) * at.dim[0] + lx;
 }
 
+// Pointer to the channel group of box point li of an atom's table.
+template <typename Real>
+__device__ __forceinline__ const Real* chi_row(const Real* chi, const AtomTab& at, int li) {
+  return chi + at.off + (long long)li * at.nchp;
+}
+
 // Exclusive block-wide scan of one int per thread (blockDim.x a multiple of 32, <= 1024).
 // Deterministic; returns the exclusive prefix and writes the block total to *total.
 __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {

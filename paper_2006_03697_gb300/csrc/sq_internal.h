@@ -36,8 +36,10 @@ struct AtomTab {
   int lo[3];        // support box corner (absolute lattice coordinates of the base image)
   int dim[3];       // support box extent
   int nch;          // channels
+  int nchp;         // channels padded to a multiple of 4 (table stride per point)
   int ch0;          // first channel in the per-channel arrays
-  long long off;    // offset of channel 0 in the table array; channel c at off + c * boxpts
+  int pad;
+  long long off;    // table offset; channel c of box point li at off + li * nchp + c
   double R[3];      // base image position (wrapped into the cell)
 };
 
@@ -89,8 +91,9 @@ struct WaveBufs {
   int* brick_n = nullptr;         // [wt][nbricks]
   void* T[3] = {nullptr, nullptr, nullptr};   // Real [wt][Upts][B]
   void* W = nullptr;              // Real [wt][3][Upts][B]
-  void* A = nullptr;              // Real [wt][r_cap][B]
-  void* P = nullptr;              // Real [wt][r_cap][B]
+  void* A = nullptr;              // Real [wt][r_cap][B]  chi_row(x_q)
+  void* P = nullptr;              // Real [wt][r_cap][B]  gamma |dOmega| chi^T t (Lanczos apply)
+  void* Pg[2] = {nullptr, nullptr};   // Real [wt][r_cap][B]  gamma |dOmega| chi^T t^j, ping-pong
   double* Spart = nullptr;        // [wt][nslab][B][9]
 };
 
@@ -98,7 +101,10 @@ struct Dev {
   double* v64 = nullptr;          // V_eff (N_d)
   float* v32 = nullptr;
   AtomTab* atoms = nullptr;       // [n_atoms]
-  double* gdv = nullptr;          // gamma * dV per channel
+  double* gdv = nullptr;          // per channel: [gamma*dV, l, m, width, rcut, 0]
+  double* gdv64 = nullptr;        // gamma * dV per channel
+  double* rcmax = nullptr;        // per atom: largest projector radius
+  float* gdv32 = nullptr;
   double* chi64 = nullptr;        // projector tables
   float* chi32 = nullptr;
   double* mom = nullptr;          // [N_d][n_pl+1][17]

@@ -29,7 +29,7 @@ __global__ void k_chi_tables(Geo g, const AtomTab* __restrict__ atoms, const dou
         const double base = pow(M_PI * w * w, -0.75) * exp(-r2 / (2.0 * w * w));
         val = (l == 0) ? base : sqrt(2.0) / w * d[mch] * base;
       }
-      chi[at.off + (long long)c * boxpts + i] = Real(val);
+      chi[at.off + (long long)i * at.nchp + c] = Real(val);
     }
   }
 }
@@ -93,9 +93,9 @@ __global__ void k_tile_entries(Geo g, Wave w, const AtomTab* __restrict__ atoms,
 }
 
 // One warp per (brick, tile): entries whose support box meets the brick, in entry order.
-__global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const TileEntry* __restrict__ entries,
-                              const int* __restrict__ n_entries, int* __restrict__ blist, int* __restrict__ bn,
-                              int* __restrict__ status) {
+__global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ rcmax,
+                              const TileEntry* __restrict__ entries, const int* __restrict__ n_entries,
+                              int* __restrict__ blist, int* __restrict__ bn, int* __restrict__ status) {
   const int br = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl), lane = threadIdx.x;
   int o[3];
   tile_origin(g, t, o);
@@ -114,11 +114,19 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
     if (e < ne) {
       const TileEntry te = ent[e];
       const AtomTab at = atoms[te.atom];
+      // the support sphere of the image meets the brick (box test on the lattice, then
+      // the distance from the image centre to the brick's bounding box against rcut)
       hit = true;
+      double d2 = 0.0;
       for (int a = 0; a < 3; ++a) {
         const int lo = at.lo[a] + te.s[a] * g.n[a], hi = lo + at.dim[a] - 1;
         hit = hit && (lo <= bhi[a]) && (hi >= bl[a]);
+        const double c = at.R[a] + te.s[a] * g.L[a];
+        const double blo = bl[a] * g.h[a], bhi_x = bhi[a] * g.h[a];
+        const double dd = (c < blo) ? blo - c : (c > bhi_x ? c - bhi_x : 0.0);
+        d2 += dd * dd;
       }
+      hit = hit && (d2 <= rcmax[te.atom] * rcmax[te.atom] * (1.0 + 1e-12) + 1e-24);
     }
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
     const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
@@ -131,17 +139,21 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
   }
 }
 
-// A[row][q] = gamma_row |dOmega| chi_row(x_q): the coefficients of w_q^T V_nl,q.
+// A[row][q] = chi_row(x_q) (w_q^T V_nl,q = sum_rows gamma |dOmega| A chi_row^T), the
+// projections of t^0 = w_q, Pg0 = gamma |dOmega| A, and a zeroed accumulator Pg1.
 template <typename Real>
 __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ chs,
                          const Real* __restrict__ chi, const TileEntry* __restrict__ entries,
-                         const int* __restrict__ n_entries, Real* __restrict__ A) {
+                         const int* __restrict__ n_entries, Real* __restrict__ A, Real* __restrict__ Pg0_,
+                         Real* __restrict__ Pg1_) {
   const int tl = blockIdx.x, t = wave_tile(w, tl);
   int o[3];
   tile_origin(g, t, o);
   const int ne = n_entries[tl];
   const TileEntry* ent = entries + (size_t)tl * g.e_cap;
   Real* At = A + (size_t)tl * g.r_cap * g.B;
+  Real* Pg0 = Pg0_ + (size_t)tl * g.r_cap * g.B;
+  Real* Pg1 = Pg1_ + (size_t)tl * g.r_cap * g.B;
   for (int i = threadIdx.x; i < ne * g.B; i += blockDim.x) {
     const int e = i / g.B, q = i % g.B;
     const TileEntry te = ent[e];
@@ -152,16 +164,19 @@ __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
     const int li = valid ? box_index(at, te.s, g.n, o[0] + qo[0], o[1] + qo[1], o[2] + qo[2]) : -1;
     const int boxpts = at.dim[0] * at.dim[1] * at.dim[2];
     for (int c = 0; c < at.nch; ++c) {
-      const double v = (li >= 0) ? chs[6 * (at.ch0 + c)] * double(chi[at.off + (long long)c * boxpts + li]) : 0.0;
-      At[(size_t)(te.row0 + c) * g.B + q] = Real(v);
+      const double x = (li >= 0) ? double(chi_row(chi, at, li)[c]) : 0.0;
+      At[(size_t)(te.row0 + c) * g.B + q] = Real(x);
+      Pg0[(size_t)(te.row0 + c) * g.B + q] = Real(chs[6 * (at.ch0 + c)] * x);   // gamma |dOmega| chi^T t^0
+      Pg1[(size_t)(te.row0 + c) * g.B + q] = Real(0);
     }
   }
 }
 
-// W_b(u, q) = sum_rows A[row][q] chi_row(u) (x_u,b - R_b) on the window of q (zero outside):
+// W_b(u, q) = sum_rows gamma |dOmega| A[row][q] chi_row(u) (x_u,b - R_b) on the window of q:
 // contracting the atom sum of the sigma^III term once, S^j_ab = sum_u W_b(u,q) (grad_a t^j)(u).
 template <typename Real>
-__global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const Real* __restrict__ chi,
+__global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ chs,
+                         const Real* __restrict__ chi,
                          const TileEntry* __restrict__ entries, const int* __restrict__ blist,
                          const int* __restrict__ bn, const Real* __restrict__ A, Real* __restrict__ W) {
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
@@ -190,10 +205,10 @@ __global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
         const AtomTab at = atoms[te.atom];
         const int li = box_index(at, te.s, g.n, ax, ay, az);
         if (li < 0) continue;
-        const int boxpts = at.dim[0] * at.dim[1] * at.dim[2];
+        const Real* cr = chi_row(chi, at, li);
         double cs = 0.0;
         for (int c = 0; c < at.nch; ++c)
-          cs += double(At[(size_t)(te.row0 + c) * g.B + q]) * double(chi[at.off + (long long)c * boxpts + li]);
+          cs += chs[6 * (at.ch0 + c)] * double(At[(size_t)(te.row0 + c) * g.B + q]) * double(cr[c]);
         if (cs == 0.0) continue;
         for (int b = 0; b < 3; ++b) acc[b] += cs * (x[b] - (at.R[b] + te.s[b] * g.L[b]));
       }
@@ -226,12 +241,13 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, Real* A, R
   k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows,
                                           h->d.status);
   SQ_LAUNCH_CHECK(h);
-  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries,
+  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
                                                           h->wb.brick_list, h->wb.brick_n, h->d.status);
   SQ_LAUNCH_CHECK(h);
-  k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A);
+  k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
+                                          (Real*)h->wb.Pg[0], (Real*)h->wb.Pg[1]);
   SQ_LAUNCH_CHECK(h);
-  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 256, 0, s>>>(g, w, h->d.atoms, chi, h->wb.entries, h->wb.brick_list,
+  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.brick_list,
                                                           h->wb.brick_n, A, W);
   SQ_LAUNCH_CHECK(h);
   k_init_t0<Real><<<1024, 256, 0, s>>>(g, w, T0);
@@ -244,7 +260,7 @@ int build_wave_entries(sq_handle* h, const Wave& w) {
   cudaStream_t s = h->stream;
   k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows, h->d.status);
   SQ_LAUNCH_CHECK(h);
-  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries,
+  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
                                                           h->wb.brick_list, h->wb.brick_n, h->d.status);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;

@@ -4,145 +4,31 @@
 // and the per-node moments rho^j, K^j_ab, N^j, S^j_ab of each column.
 //
 // Kernels (Real = double for SQ_FP64, float for SQ_MIXED; node sums always FP64):
-//   k_stencil   one block per (z-slab of 4 planes, tile): H t^j on the union window, the
-//               window mask, the recurrence update, and the fused nonlocal-stress partial
-//               sum_u W_b (grad_a t^j) (the grad taps reuse the Laplacian's loads).
-//   k_project   one block per (atom image, tile): P[row][q] = chi_row^T t^{j+1}.
-//   k_moments   one warp per node: rho^j, K^j (restricted grad_a grad_b at the node),
-//               N^j = sum_rows A P, S^j = sum of the slab partials; FP64 table row.
+//   k_step      one block per (z-slab of 4 planes, tile); one warp = 4 x-adjacent points x the
+//               8 nodes of the tile, so a warp's points share one 4^3 brick and its list of
+//               atom images. Per element: Laplacian + V + nonlocal apply (from Pg^j), the
+//               window mask and the recurrence update; the nonlocal-stress partial
+//               sum_u W_b (grad_a t^j) (the gradient taps reuse the Laplacian loads); and,
+//               fused, the projections gamma |dOmega| chi^T t^{j+1} of the new column
+//               (warp shuffles over the 4 points, shared-memory accumulation per slab,
+//               one global add per row and node).
+//   k_moments   one block per tile: rho^j, K^j (restricted grad_a grad_b at the node),
+//               N^j = sum_rows chi(x_q) Pg^j, S^j = sum of the slab partials; FP64 table
+//               row; then clears Pg^j, which accumulates the projections of step j + 1.
+//   k_apply_h / k_project   plain H_q v for the Lanczos bounds (FP64).
 #include <algorithm>
 
 #include "sq_device.cuh"
 
 namespace sq {
 
-template <typename Real>
-struct Coef {
-  Real ca, cb, cc;
-};
-
-template <typename Real>
-__global__ void __launch_bounds__(kThreads)
-k_stencil(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
-          const Real* __restrict__ P, const Real* __restrict__ Wt, const Real* __restrict__ chi,
-          const AtomTab* __restrict__ atoms, const double* __restrict__ chs, const TileEntry* __restrict__ entries,
-          const int* __restrict__ blist, const int* __restrict__ bn, const Real* __restrict__ v,
-          const double* __restrict__ scal, int mode, double* __restrict__ Spart) {
-  // mode 0: t^1 = Hhat t^0;  mode 1: t^{j+1} = 2 Hhat t^j - t^{j-1};  mode 2: moments only;
-  // mode 3: Tn = H_q t (restricted, unscaled; used by the Lanczos bounds)
-  const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
-  int o[3];
-  tile_origin(g, t, o);
-  // step coefficients 2/zeta and -2 chi/zeta (halved for t^1 = Hhat t^0)
-  const double f = (mode == 0) ? 0.5 : 1.0;
-  const Real ca = Real(f * scal[4]), cb = Real(f * scal[5]), cc = Real(mode == 0 ? 0.0 : 1.0);
-  const int Ux = g.U[0], Uy = g.U[1], Uz = g.U[2], B = g.B;
-  const size_t tbase = (size_t)tl * g.Upts * B;
-  const Real* T = Tc + tbase;
-  const Real* Pt = P + (size_t)tl * g.r_cap * B;
-  const TileEntry* ent = entries + (size_t)tl * g.e_cap;
-  const int z0 = slab * kBrick, nz = min(kBrick, Uz - z0);
-  const int nel = Ux * Uy * nz * B;
-  const int sx = B, sy = Ux * B, sz = Ux * Uy * B;
-
-  Real lap[3][kMaxNo + 1], grd[3][kMaxNo + 1];
-  for (int a = 0; a < 3; ++a)
-    for (int p = 0; p <= kMaxNo; ++p) {
-      lap[a][p] = Real(g.lap[a][p]);
-      grd[a][p] = Real(g.grd[a][p]);
-    }
-  const Real lap0 = Real(g.lap0);
-
-  const int q = threadIdx.x % B;   // kThreads is a multiple of B: each thread keeps one node
-  int qo[3];
-  node_offset(g, q, qo);
-  const bool valid = node_valid(g, o, qo);
-  Real sacc[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) sacc[k] = Real(0);
-
-  for (int i = threadIdx.x; i < nel; i += kThreads) {
-    const int p = i / B;
-    const int ux = p % Ux, uy = (p / Ux) % Uy, uz = z0 + p / (Ux * Uy);
-    const int pt = (uz * Uy + uy) * Ux + ux;
-    const size_t e = (size_t)pt * B + q;
-    if (!valid || !in_window(g, qo, ux, uy, uz)) {
-      if (mode != 2) Tn[tbase + e] = Real(0);
-      continue;
-    }
-    const Real tc = T[e];
-    Real y = lap0 * tc;
-    Real gr[3] = {Real(0), Real(0), Real(0)};
-    const int u[3] = {ux, uy, uz};
-    const int st[3] = {sx, sy, sz};
-    const int Ua[3] = {Ux, Uy, Uz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      for (int pp = 1; pp <= g.n_o; ++pp) {
-        const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
-        const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
-        y += lap[a][pp] * (fp + fm);
-        gr[a] += grd[a][pp] * (fp - fm);
-      }
-    }
-    const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
-    {
-      int wx = ax % g.n[0]; if (wx < 0) wx += g.n[0];
-      int wy = ay % g.n[1]; if (wy < 0) wy += g.n[1];
-      int wz = az % g.n[2]; if (wz < 0) wz += g.n[2];
-      y += v[(wz * g.n[1] + wy) * g.n[0] + wx] * tc;
-    }
-    // nonlocal: sum over atom images covering this point of gamma |dOmega| chi(u) P[row][q]
-    {
-      const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
-      const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
-      const int nb = bn[(size_t)tl * g.nbricks + br];
-      for (int k = 0; k < nb; ++k) {
-        const TileEntry te = ent[lst[k]];
-        const AtomTab at = atoms[te.atom];
-        const int li = box_index(at, te.s, g.n, ax, ay, az);
-        if (li < 0) continue;
-        const int boxpts = at.dim[0] * at.dim[1] * at.dim[2];
-        for (int c = 0; c < at.nch; ++c)
-          y += Real(chs[6 * (at.ch0 + c)]) * chi[at.off + (long long)c * boxpts + li] * Pt[(size_t)(te.row0 + c) * B + q];
-      }
-    }
-    if (mode == 3) {          // plain H t (Lanczos)
-      Tn[tbase + e] = y;
-      continue;
-    }
-    if (mode != 2) {
-      const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
-      Tn[tbase + e] = ca * y + cb * tc - cc * tp;
-    }
-    // S^j_ab partial: W_b(u, q) (grad_a t^j)(u)
-    const Real* Wq = Wt + (size_t)tl * 3 * g.Upts * B;
-    const Real w0 = Wq[e], w1 = Wq[(size_t)g.Upts * B + e], w2 = Wq[(size_t)2 * g.Upts * B + e];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      sacc[3 * a + 0] += gr[a] * w0;
-      sacc[3 * a + 1] += gr[a] * w1;
-      sacc[3 * a + 2] += gr[a] * w2;
-    }
-  }
-  if (mode == 3) return;
-  // deterministic block reduction per node: threads q, q + B, q + 2B, ... in order
-  __shared__ double red[kThreads][9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) red[threadIdx.x][k] = double(sacc[k]);
-  __syncthreads();
-  for (int k2 = threadIdx.x; k2 < B * 9; k2 += kThreads) {
-    const int qq = k2 / 9, k = k2 % 9;
-    double s = 0.0;
-    for (int th = qq; th < kThreads; th += B) s += red[th][k];
-    Spart[(((size_t)tl * g.nslab + slab) * B + qq) * 9 + k] = s;
-  }
-}
-
+// ------------------------------------------------------------------------------ Lanczos apply
+// P[row][q] = gamma |dOmega| chi_row^T v (one block per atom image of a tile)
 template <typename Real>
 __global__ void __launch_bounds__(kThreads)
 k_project(Geo g, Wave w, const Real* __restrict__ Tn, const Real* __restrict__ chi, const AtomTab* __restrict__ atoms,
-          const TileEntry* __restrict__ entries, const int* __restrict__ n_entries, Real* __restrict__ P) {
+          const double* __restrict__ chs, const TileEntry* __restrict__ entries, const int* __restrict__ n_entries,
+          Real* __restrict__ P) {
   const int eidx = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
   if (eidx >= n_entries[tl]) return;
   int o[3];
@@ -158,21 +44,20 @@ k_project(Geo g, Wave w, const Real* __restrict__ Tn, const Real* __restrict__ c
   }
   const int nx = max(0, hi[0] - lo[0]), ny = max(0, hi[1] - lo[1]), nzz = max(0, hi[2] - lo[2]);
   const int nel = nx * ny * nzz * B;
-  const int boxpts = at.dim[0] * at.dim[1] * at.dim[2];
   const Real* T = Tn + (size_t)tl * g.Upts * B;
-  const int q = threadIdx.x % B;
   Real acc[kMaxCh];
 #pragma unroll
   for (int c = 0; c < kMaxCh; ++c) acc[c] = Real(0);
   for (int i = threadIdx.x; i < nel; i += kThreads) {
-    const int p = i / B;
+    const int p = i / B, q = i % B;
     const int lx = lo[0] + p % nx, ly = lo[1] + (p / nx) % ny, lz = lo[2] + p / (nx * ny);
     const Real tv = T[((size_t)(lz * g.U[1] + ly) * g.U[0] + lx) * B + q];
     if (tv == Real(0)) continue;
     const int li = box_index(at, te.s, g.n, o[0] - g.m[0] + lx, o[1] - g.m[1] + ly, o[2] - g.m[2] + lz);
+    const Real* cr = chi_row(chi, at, li);
 #pragma unroll
     for (int c = 0; c < kMaxCh; ++c)
-      if (c < at.nch) acc[c] += chi[at.off + (long long)c * boxpts + li] * tv;
+      if (c < at.nch) acc[c] += cr[c] * tv;
   }
   __shared__ double red[kThreads][kMaxCh];
 #pragma unroll
@@ -183,15 +68,253 @@ k_project(Geo g, Wave w, const Real* __restrict__ Tn, const Real* __restrict__ c
     const int qq = k2 % B, c = k2 / B;
     double s = 0.0;
     for (int th = qq; th < kThreads; th += B) s += red[th][c];
-    Pt[(size_t)(te.row0 + c) * B + qq] = Real(s);
+    Pt[(size_t)(te.row0 + c) * B + qq] = Real(s * chs[6 * (at.ch0 + c)]);
+  }
+}
+
+// out = H_q v on every node window of the wave (zero outside the windows); P from k_project.
+template <typename Real>
+__global__ void __launch_bounds__(kThreads)
+k_apply_h(Geo g, Wave w, const Real* __restrict__ Tc, Real* __restrict__ Tn, const Real* __restrict__ P,
+          const Real* __restrict__ chi, const AtomTab* __restrict__ atoms, const TileEntry* __restrict__ entries,
+          const int* __restrict__ blist, const int* __restrict__ bn, const Real* __restrict__ v) {
+  const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
+  int o[3];
+  tile_origin(g, t, o);
+  const int Ux = g.U[0], Uy = g.U[1], Uz = g.U[2], B = g.B;
+  const size_t tbase = (size_t)tl * g.Upts * B;
+  const Real* T = Tc + tbase;
+  const Real* Pt = P + (size_t)tl * g.r_cap * B;
+  const TileEntry* ent = entries + (size_t)tl * g.e_cap;
+  const int z0 = slab * kBrick, nz = min(kBrick, Uz - z0);
+  const int nel = Ux * Uy * nz * B;
+  const int st[3] = {B, Ux * B, Ux * Uy * B};
+  const int Ua[3] = {Ux, Uy, Uz};
+  for (int i = threadIdx.x; i < nel; i += kThreads) {
+    const int p = i / B, q = i % B;
+    int qo[3];
+    node_offset(g, q, qo);
+    const int ux = p % Ux, uy = (p / Ux) % Uy, uz = z0 + p / (Ux * Uy);
+    const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * B + q;
+    if (!node_valid(g, o, qo) || !in_window(g, qo, ux, uy, uz)) {
+      Tn[tbase + e] = Real(0);
+      continue;
+    }
+    const Real tc = T[e];
+    Real y = Real(g.lap0) * tc;
+    const int u[3] = {ux, uy, uz};
+    for (int a = 0; a < 3; ++a)
+      for (int pp = 1; pp <= g.n_o; ++pp) {
+        const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
+        const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
+        y += Real(g.lap[a][pp]) * (fp + fm);
+      }
+    const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
+    int wx = ax % g.n[0]; if (wx < 0) wx += g.n[0];
+    int wy = ay % g.n[1]; if (wy < 0) wy += g.n[1];
+    int wz = az % g.n[2]; if (wz < 0) wz += g.n[2];
+    y += v[(wz * g.n[1] + wy) * g.n[0] + wx] * tc;
+    const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
+    const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
+    const int nb = bn[(size_t)tl * g.nbricks + br];
+    for (int k = 0; k < nb; ++k) {
+      const TileEntry te = ent[lst[k]];
+      const AtomTab at = atoms[te.atom];
+      const int li = box_index(at, te.s, g.n, ax, ay, az);
+      if (li < 0) continue;
+      const Real* cr = chi_row(chi, at, li);
+      for (int c = 0; c < at.nch; ++c) y += cr[c] * Pt[(size_t)(te.row0 + c) * B + q];
+    }
+    Tn[tbase + e] = y;
+  }
+}
+
+// ------------------------------------------------------------------------------ sweep step
+template <typename Real> struct V4;
+template <> struct V4<float> { using T = float4; };
+template <> struct V4<double> { using T = double4; };
+
+template <typename Real>
+__device__ __forceinline__ void load4(const Real* p, Real out[4]) {
+  const typename V4<Real>::T x = *reinterpret_cast<const typename V4<Real>::T*>(p);
+  out[0] = x.x;
+  out[1] = x.y;
+  out[2] = x.z;
+  out[3] = x.w;
+}
+
+constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x 8 nodes
+
+// mode 0: t^1 = Hhat t^0;  mode 1: t^{j+1} = 2 Hhat t^j - t^{j-1};  mode 2: moments only
+template <typename Real, int NO>
+__global__ void __launch_bounds__(kThreads)
+k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
+       const Real* __restrict__ Pg, Real* __restrict__ Pg_next, const Real* __restrict__ Wt,
+       const Real* __restrict__ chi, const AtomTab* __restrict__ atoms, const Real* __restrict__ gdv,
+       const TileEntry* __restrict__ entries, const int* __restrict__ n_rows, const int* __restrict__ blist,
+       const int* __restrict__ bn, const Real* __restrict__ v, const double* __restrict__ scal, int mode,
+       double* __restrict__ Spart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* Ps = reinterpret_cast<Real*>(smem_raw);             // [rows][8] projections of this slab
+  __shared__ double red[kThreads][9];
+  const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int o[3];
+  tile_origin(g, t, o);
+  const double f = (mode == 0) ? 0.5 : 1.0;
+  const Real ca = Real(f * scal[4]), cb = Real(f * scal[5]), cc = Real(mode == 0 ? 0.0 : 1.0);
+  const int Ux = g.U[0], Uy = g.U[1], Uz = g.U[2];
+  const size_t tbase = (size_t)tl * g.Upts * kTileB;
+  const Real* T = Tc + tbase;
+  const Real* Pt = Pg + (size_t)tl * g.r_cap * kTileB;
+  const TileEntry* ent = entries + (size_t)tl * g.e_cap;
+  const int nrows = n_rows[tl];
+  const bool project = (mode != 2);
+  const int z0 = slab * kBrick, nz = min(kBrick, Uz - z0);
+  const int nel = Ux * Uy * nz * kTileB;                    // multiple of 32 (Ux % 4 == 0)
+  const int st[3] = {kTileB, Ux * kTileB, Ux * Uy * kTileB};
+  const int Ua[3] = {Ux, Uy, Uz};
+
+  Real lap[3][NO + 1], grd[3][NO + 1];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int p = 1; p <= NO; ++p) {
+      lap[a][p] = Real(g.lap[a][p]);
+      grd[a][p] = Real(g.grd[a][p]);
+    }
+  const Real lap0 = Real(g.lap0);
+
+  if (project)
+    for (int i = threadIdx.x; i < nrows * kTileB; i += kThreads) Ps[i] = Real(0);
+  __syncthreads();
+
+  const int q = lane & 7;
+  int qo[3];
+  qo[0] = q & 1;
+  qo[1] = (q >> 1) & 1;
+  qo[2] = q >> 2;
+  const bool valid = node_valid(g, o, qo);
+  const Real* Wq = Wt + (size_t)tl * 3 * g.Upts * kTileB;
+  const size_t wstr = (size_t)g.Upts * kTileB;
+  Real sacc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) sacc[k] = Real(0);
+
+  for (int base = warp * 32; base < nel; base += kThreads) {
+    const int i = base + lane;
+    const int p = i >> 3;
+    const int ux = p % Ux, uy = (p / Ux) % Uy, uz = z0 + p / (Ux * Uy);
+    const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + q;
+    const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
+    // the warp's 4 points lie in one brick: its entry list is warp-uniform
+    const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
+    const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
+    const int nb = bn[(size_t)tl * g.nbricks + br];
+    const bool inwin = valid && in_window(g, qo, ux, uy, uz);
+    Real tn = Real(0);
+    if (inwin) {
+      const Real tc = T[e];
+      Real y = lap0 * tc;
+      Real gr[3];
+      const int u[3] = {ux, uy, uz};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        gr[a] = Real(0);
+#pragma unroll
+        for (int pp = 1; pp <= NO; ++pp) {
+          const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
+          const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
+          y += lap[a][pp] * (fp + fm);
+          gr[a] += grd[a][pp] * (fp - fm);
+        }
+      }
+      {
+        int wx = ax % g.n[0]; if (wx < 0) wx += g.n[0];
+        int wy = ay % g.n[1]; if (wy < 0) wy += g.n[1];
+        int wz = az % g.n[2]; if (wz < 0) wz += g.n[2];
+        y += v[(wz * g.n[1] + wy) * g.n[0] + wx] * tc;
+      }
+      for (int k = 0; k < nb; ++k) {
+        const TileEntry te = ent[lst[k]];
+        const AtomTab at = atoms[te.atom];
+        const int li = box_index(at, te.s, g.n, ax, ay, az);
+        if (li < 0) continue;
+        const Real* cr = chi_row(chi, at, li);
+        const Real* pr = Pt + (size_t)te.row0 * kTileB + q;
+        for (int c0 = 0; c0 < at.nch; c0 += 4) {
+          Real cv[4];
+          load4(cr + c0, cv);
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c0 + c < at.nch) y += cv[c] * pr[(c0 + c) * kTileB];
+        }
+      }
+      if (mode != 2) {
+        const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
+        tn = ca * y + cb * tc - cc * tp;
+        Tn[tbase + e] = tn;
+      }
+      const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sacc[3 * a + 0] += gr[a] * w0;
+        sacc[3 * a + 1] += gr[a] * w1;
+        sacc[3 * a + 2] += gr[a] * w2;
+      }
+    } else if (mode != 2) {
+      Tn[tbase + e] = Real(0);
+    }
+    // projections of t^{j+1}: gamma |dOmega| chi_row(u) t^{j+1}(u, q), summed over the warp's
+    // 4 points by shuffles, accumulated per slab in shared memory
+    if (project && __any_sync(0xffffffffu, tn != Real(0))) {
+      for (int k = 0; k < nb; ++k) {
+        const TileEntry te = ent[lst[k]];
+        const AtomTab at = atoms[te.atom];
+        const int li = (tn != Real(0)) ? box_index(at, te.s, g.n, ax, ay, az) : -1;
+        if (!__any_sync(0xffffffffu, li >= 0)) continue;
+        for (int c0 = 0; c0 < at.nch; c0 += 4) {
+          Real cv[4] = {Real(0), Real(0), Real(0), Real(0)};
+          if (li >= 0) load4(chi_row(chi, at, li) + c0, cv);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (c0 + c < at.nch) {
+              Real s = cv[c] * tn;
+              s += __shfl_xor_sync(0xffffffffu, s, 8);
+              s += __shfl_xor_sync(0xffffffffu, s, 16);
+              if (lane < 8 && s != Real(0))
+                atomicAdd(&Ps[(te.row0 + c0 + c) * kTileB + lane], s * gdv[at.ch0 + c0 + c]);
+            }
+          }
+        }
+      }
+    }
+  }
+  // S partials: fixed-order block reduction per node
+#pragma unroll
+  for (int k = 0; k < 9; ++k) red[threadIdx.x][k] = double(sacc[k]);
+  __syncthreads();
+  for (int k2 = threadIdx.x; k2 < kTileB * 9; k2 += kThreads) {
+    const int qq = k2 / 9, k = k2 % 9;
+    double s = 0.0;
+    for (int th = qq; th < kThreads; th += kTileB) s += red[th][k];
+    Spart[(((size_t)tl * g.nslab + slab) * kTileB + qq) * 9 + k] = s;
+  }
+  if (project) {
+    Real* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
+    for (int idx = threadIdx.x; idx < nrows * kTileB; idx += kThreads) {
+      const Real s = Ps[idx];
+      if (s != Real(0)) atomicAdd(&Pn[idx], s);
+    }
   }
 }
 
 __constant__ int c_kpairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
 
+// Moments of t^j per node (one warp per node), then Pg^j := 0 (the accumulator of step j + 1).
 template <typename Real>
 __global__ void __launch_bounds__(kThreads)
-k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restrict__ A, const Real* __restrict__ P,
+k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restrict__ A, Real* __restrict__ Pg,
           const int* __restrict__ n_rows, const double* __restrict__ Spart, double* __restrict__ mom) {
   const int tl = blockIdx.x, t = wave_tile(w, tl);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -200,7 +323,7 @@ k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restr
   const int B = g.B;
   const Real* T = Tj + (size_t)tl * g.Upts * B;
   const Real* At = A + (size_t)tl * g.r_cap * B;
-  const Real* Pt = P + (size_t)tl * g.r_cap * B;
+  Real* Pt = Pg + (size_t)tl * g.r_cap * B;
   const int nr = n_rows[tl];
   for (int q = warp; q < B; q += kThreads / 32) {
     int qo[3];
@@ -236,6 +359,7 @@ k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restr
       }
       out[1 + pr] = warp_sum(term);
     }
+    // N^j = w_q^T V_nl,q t^j = sum_rows chi_row(x_q) (gamma |dOmega| chi_row^T t^j)
     double nacc = 0.0;
     for (int r = lane; r < nr; r += 32) nacc += double(At[(size_t)r * B + q]) * double(Pt[(size_t)r * B + q]);
     out[7] = warp_sum(nacc);
@@ -251,20 +375,57 @@ k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restr
       mom[((size_t)node * (g.n_pl + 1) + j) * SQ_N_MOMENTS + lane] = val;
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr * B; i += kThreads) Pt[i] = Real(0);
+}
+
+template <typename Real, int NO>
+static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
+                       const Real* Pg, Real* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
+                       int mode) {
+  if (smem > 48 * 1024)
+    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  k_step<Real, NO><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.atoms, gdv,
+                                                        h->wb.entries, h->wb.n_rows, h->wb.brick_list, h->wb.brick_n, v,
+                                                        h->d.scal, mode, h->wb.Spart);
+  SQ_LAUNCH_CHECK(h);
+  return SQ_OK;
 }
 
 template <typename Real>
-static int sweep_t(sq_handle* h, const Real* chi, const Real* v) {
+static int dispatch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
+                         const Real* Pg, Real* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
+                         int mode) {
+  switch (h->geo.n_o) {
+    case 1: return launch_step<Real, 1>(h, w, grid, smem, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, v, mode);
+    case 2: return launch_step<Real, 2>(h, w, grid, smem, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, v, mode);
+    case 3: return launch_step<Real, 3>(h, w, grid, smem, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, v, mode);
+    case 4: return launch_step<Real, 4>(h, w, grid, smem, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, v, mode);
+    case 5: return launch_step<Real, 5>(h, w, grid, smem, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, v, mode);
+    default: return launch_step<Real, 6>(h, w, grid, smem, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, v, mode);
+  }
+}
+
+template <typename Real>
+static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
   Real* T[3] = {(Real*)h->wb.T[0], (Real*)h->wb.T[1], (Real*)h->wb.T[2]};
-  Real* P = (Real*)h->wb.P;
+  Real* Pg[2] = {(Real*)h->wb.Pg[0], (Real*)h->wb.Pg[1]};
   Real* A = (Real*)h->wb.A;
   Real* W = (Real*)h->wb.W;
+  std::vector<int> nrows;
   for (const Wave& w : h->waves) {
     int rc = build_wave_lists(h, w);
     if (rc != SQ_OK) return rc;
-    const dim3 gstencil(g.nslab, w.ntiles), gproj(g.e_cap, w.ntiles);
+    // largest projector-row count of the wave sizes the per-slab shared accumulator
+    nrows.resize(w.ntiles);
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(nrows.data(), h->wb.n_rows, sizeof(int) * w.ntiles, cudaMemcpyDeviceToHost, s));
+    SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+    const int rmax = nrows.empty() ? 0 : *std::max_element(nrows.begin(), nrows.end());
+    const size_t smem = std::max<size_t>(16, size_t(rmax) * kTileB * sizeof(Real));
+    if (smem > 200 * 1024) return fail(h, SQ_ERR_INVALID_ARG, "too many projector rows per tile for shared memory");
+    const dim3 gstencil(g.nslab, w.ntiles);
     // algorithmic bytes of one stencil launch: node columns x region points x vectors moved
     long long nodes = 0;
     for (int tl = 0; tl < w.ntiles; ++tl) {
@@ -274,32 +435,20 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v) {
       nodes += (long long)std::min(g.b, g.n[0] - o[0]) * std::min(g.b, g.n[1] - o[1]) * std::min(g.b, g.n[2] - o[2]);
     }
     const double col_bytes = double(nodes) * (2 * g.m[0] + 1) * (2 * g.m[1] + 1) * (2 * g.m[2] + 1) * sizeof(Real);
-    cudaEvent_t ev = timing_begin(h, SQ_K_PROJECT, 0.0);
-    k_project<Real><<<gproj, kThreads, 0, s>>>(g, w, T[0], chi, h->d.atoms, h->wb.entries, h->wb.n_entries, P);
-    timing_end(h, ev);
-    SQ_LAUNCH_CHECK(h);
     for (int j = 0; j <= g.n_pl; ++j) {
       Real* Tc = T[j % 3];
       Real* Tn = T[(j + 1) % 3];
       Real* Tp = T[(j + 2) % 3];
       const int mode = (j == g.n_pl) ? 2 : (j == 0 ? 0 : 1);
       const double vecs = (mode == 0) ? 2.0 : (mode == 1) ? 3.0 : 1.0;   // reads t^j (t^{j-1}), writes t^{j+1}
-      ev = timing_begin(h, SQ_K_STENCIL, vecs * col_bytes);
-      k_stencil<Real><<<gstencil, kThreads, 0, s>>>(g, w, Tc, Tp, Tn, P, W, chi, h->d.atoms, h->d.gdv, h->wb.entries,
-                                                     h->wb.brick_list, h->wb.brick_n, v, h->d.scal, mode,
-                                                     h->wb.Spart);
+      cudaEvent_t ev = timing_begin(h, SQ_K_STENCIL, vecs * col_bytes);
+      rc = dispatch_step<Real>(h, w, gstencil, smem, Tc, Tp, Tn, Pg[j % 2], Pg[(j + 1) % 2], W, chi, gdv, v, mode);
+      if (rc != SQ_OK) return rc;
       timing_end(h, ev);
-      SQ_LAUNCH_CHECK(h);
       ev = timing_begin(h, SQ_K_MOMENTS, 0.0);
-      k_moments<Real><<<w.ntiles, kThreads, 0, s>>>(g, w, j, Tc, A, P, h->wb.n_rows, h->wb.Spart, h->d.mom);
+      k_moments<Real><<<w.ntiles, kThreads, 0, s>>>(g, w, j, Tc, A, Pg[j % 2], h->wb.n_rows, h->wb.Spart, h->d.mom);
       timing_end(h, ev);
       SQ_LAUNCH_CHECK(h);
-      if (j < g.n_pl) {
-        ev = timing_begin(h, SQ_K_PROJECT, 0.0);
-        k_project<Real><<<gproj, kThreads, 0, s>>>(g, w, Tn, chi, h->d.atoms, h->wb.entries, h->wb.n_entries, P);
-        timing_end(h, ev);
-        SQ_LAUNCH_CHECK(h);
-      }
     }
   }
   {
@@ -316,19 +465,18 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v) {
 int launch_apply_h64(sq_handle* h, const Wave& w, const double* v, double* out, double* P) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  k_project<double><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, h->d.chi64, h->d.atoms, h->wb.entries,
-                                                                  h->wb.n_entries, P);
+  k_project<double><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, h->d.chi64, h->d.atoms, h->d.gdv,
+                                                                  h->wb.entries, h->wb.n_entries, P);
   SQ_LAUNCH_CHECK(h);
-  k_stencil<double><<<dim3(g.nslab, w.ntiles), kThreads, 0, s>>>(g, w, v, nullptr, out, P, nullptr, h->d.chi64,
-                                                                  h->d.atoms, h->d.gdv, h->wb.entries, h->wb.brick_list,
-                                                                  h->wb.brick_n, h->d.v64, h->d.scal, 3, nullptr);
+  k_apply_h<double><<<dim3(g.nslab, w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, h->d.chi64, h->d.atoms, h->wb.entries,
+                                                                  h->wb.brick_list, h->wb.brick_n, h->d.v64);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }
 
 int run_sweep(sq_handle* h) {
-  if (h->precision == SQ_FP64) return sweep_t<double>(h, h->d.chi64, h->d.v64);
-  return sweep_t<float>(h, h->d.chi32, h->d.v32);
+  if (h->precision == SQ_FP64) return sweep_t<double>(h, h->d.chi64, h->d.v64, h->d.gdv64);
+  return sweep_t<float>(h, h->d.chi32, h->d.v32, h->d.gdv32);
 }
 
 }  // namespace sq
