@@ -252,7 +252,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
     const int k = d->lanczos_k > 0 ? d->lanczos_k : 40;
     const size_t nst = P.lz_tiles.size();
     P.fixed_bytes += sizeof(double) * (size_t(k + 2) * nst * g.Upts * g.B + nst * size_t(g.r_cap) * g.B +
-                                       nst * g.B * size_t(4 * k + 8)) + sizeof(int) * nst;
+                                       nst * g.B * size_t(5 * k + 8)) + sizeof(int) * nst;
     P.fixed_bytes += sizeof(double) * size_t(P.table_len);   // FP64 tables for the Lanczos apply
   }
   // tiles per wave: keep the per-wave working set near 8 GiB
@@ -445,7 +445,7 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
     SQ_ALLOC(h->d.lzV, sizeof(double) * size_t(k + 1) * nst * g.Upts * g.B);
     SQ_ALLOC(h->d.lzW, sizeof(double) * nst * g.Upts * g.B);
     SQ_ALLOC(h->d.lzP, sizeof(double) * nst * size_t(g.r_cap) * g.B);
-    SQ_ALLOC(h->d.lzC, sizeof(double) * nst * g.B * size_t(4 * k + 8));
+    SQ_ALLOC(h->d.lzC, sizeof(double) * nst * g.B * size_t(5 * k + 8));
     SQ_ALLOC(h->d.lz_tiles, sizeof(int) * nst);
   }
 #undef SQ_ALLOC

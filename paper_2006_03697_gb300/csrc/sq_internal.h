@@ -180,7 +180,7 @@ int fail(sq_handle* h, int code, const std::string& msg);
     (h)->launches++;                                                                      \
     cudaError_t e_ = cudaGetLastError();                                                  \
     if (e_ != cudaSuccess)                                                                \
-      return ::sq::fail((h), SQ_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+      return ::sq::fail((h), SQ_ERR_CUDA, std::string("kernel launch (") + __FILE__ + ":" + std::to_string(__LINE__) + "): " + cudaGetErrorString(e_)); \
   } while (0)
 
 int dev_alloc(sq_handle* h, void** p, size_t bytes);

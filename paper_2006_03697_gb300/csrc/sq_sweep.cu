@@ -383,8 +383,8 @@ template <typename Real, int NO>
 static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
                        const Real* Pg, Real* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                        int mode) {
-  if (smem > 48 * 1024)
-    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  // the kernel also holds a static [kThreads][9] double array: always opt in to the dynamic size
+  SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   k_step<Real, NO><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.atoms, gdv,
                                                         h->wb.entries, h->wb.n_rows, h->wb.brick_list, h->wb.brick_n, v,
                                                         h->d.scal, mode, h->wb.Spart);
@@ -424,7 +424,8 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
     SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
     const int rmax = nrows.empty() ? 0 : *std::max_element(nrows.begin(), nrows.end());
     const size_t smem = std::max<size_t>(16, size_t(rmax) * kTileB * sizeof(Real));
-    if (smem > 200 * 1024) return fail(h, SQ_ERR_INVALID_ARG, "too many projector rows per tile for shared memory");
+    if (smem + sizeof(double) * kThreads * 9 > 220 * 1024)
+      return fail(h, SQ_ERR_INVALID_ARG, "too many projector rows per tile for shared memory");
     const dim3 gstencil(g.nslab, w.ntiles);
     // algorithmic bytes of one stencil launch: node columns x region points x vectors moved
     long long nodes = 0;
