@@ -169,6 +169,28 @@ int sq_kernel_timing(sq_handle* h, int enable);
 int sq_kernel_timing_read(const sq_handle* h, int kid, long long* launches, double* total_ms,
                           double* algo_bytes);
 
+/* Fermi level without any device allocation. The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc (an allocator that is locked or at its
+ * budget, a plug-in that must leave the process's device heap alone). It runs the same
+ * bisection as sq_fermi_level on a moment table the caller owns:
+ *   mom_dev      device, [n_nodes][n_pl + 1][SQ_N_MOMENTS] FP64 (the sq_moments_copy layout;
+ *                only slot 0, rho^j, is read)
+ *   lambda_lo/hi the spectral bounds the table was computed with (sq_get_bounds)
+ *   kT, n_e      smearing and electron count; cheb_quad_M <= 0 selects 2048
+ *   stream       cudaStream_t or NULL; the call is asynchronous on it
+ *   mu_dev       device, 1 double: receives mu, or NaN when N(mu) - N_e has no sign change
+ * Its scratch (node sums and cosine sums) lives in one fixed file-scope device array of
+ * (SQ_NOALLOC_MAX_NPL + 1 + SQ_NOALLOC_MAX_M + 32) doubles (about 73 KB) that every GPU
+ * loading the library holds until exit; n_pl > SQ_NOALLOC_MAX_NPL or M > SQ_NOALLOC_MAX_M is
+ * rejected with SQ_ERR_INVALID_ARG. No cudaMalloc / cudaFree or allocating library call is
+ * made. The first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture. Every call rewrites the whole
+ * scratch; calls that overlap on the GPU share it and race. */
+#define SQ_NOALLOC_MAX_NPL 1024
+#define SQ_NOALLOC_MAX_M 8192
+int sq_fermi_level_noalloc(const double* mom_dev, int n_nodes, int n_pl, double lambda_lo, double lambda_hi,
+                           double kT, double n_e, int cheb_quad_M, void* stream, double* mu_dev);
+
 void sq_destroy(sq_handle* h);
 
 /* Last error text of h (or of the last failed sq_setup when h is NULL); never NULL. */

@@ -29,7 +29,7 @@ SQ_N_MOMENTS = 17
 EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
-    "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_destroy", "sq_last_error",
+    "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_destroy", "sq_last_error",
 ]
 SQ_K_STENCIL = 0
 SQ_K_PROJECT = 1
@@ -91,6 +91,9 @@ def lib():
         L.sq_kernel_timing_read.argtypes = [H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
         L.sq_kernel_timing_read.restype = C.c_int
+        L.sq_fermi_level_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                             C.c_double, C.c_int, C.c_void_p, C.c_void_p]
+        L.sq_fermi_level_noalloc.restype = C.c_int
         L.sq_destroy.argtypes = [H]
         L.sq_destroy.restype = None
         L.sq_last_error.argtypes = [H]
@@ -215,6 +218,16 @@ def sq_kernel_timing_read(h, kid: int):
     n, ms, b = C.c_longlong(), C.c_double(), C.c_double()
     _check(lib().sq_kernel_timing_read(h, kid, C.byref(n), C.byref(ms), C.byref(b)), h)
     return n.value, ms.value, b.value
+
+
+def sq_fermi_level_noalloc(mom_dev_ptr: int, n_nodes: int, n_pl: int, lambda_lo: float, lambda_hi: float,
+                           kT: float, n_e: float, cheb_quad_M: int, stream, mu_dev_ptr: int):
+    """Asynchronous; mu lands in the caller's device double at mu_dev_ptr."""
+    rc = lib().sq_fermi_level_noalloc(mom_dev_ptr, n_nodes, n_pl, lambda_lo, lambda_hi, kT, n_e, cheb_quad_M,
+                                      stream, mu_dev_ptr)
+    if rc != SQ_OK:
+        raise SQError(rc, "sq_fermi_level_noalloc rejected its arguments" if rc == SQ_ERR_INVALID_ARG
+                      else "CUDA error in sq_fermi_level_noalloc")
 
 
 def sq_destroy(h):
