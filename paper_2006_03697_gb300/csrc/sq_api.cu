@@ -207,6 +207,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
     P.atoms.push_back(at);
   }
   P.table_len = off;
+  if (off >= (1ll << 31)) { why = "projector tables exceed 2^31 entries"; return SQ_ERR_INVALID_ARG; }
   g.e_cap = int(std::max<long long>(1, std::min<long long>(e_cap, 1 << 20)));
   g.r_cap = int(std::max<long long>(1, std::min<long long>(r_cap, 1 << 22)));
   g.br_cap = int(std::max<long long>(1, std::min<long long>(br_cap, g.e_cap)));
@@ -216,6 +217,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   size_t tileB = size_t(g.B);
   P.per_tile_bytes = size_t(g.e_cap) * sizeof(sq::TileEntry) + 2 * sizeof(int) +
                      size_t(g.nbricks) * (size_t(g.br_cap) + 1) * sizeof(int) +
+                     size_t(g.nbricks) * size_t(g.br_cap) * 2 * sizeof(int4) +
                      3 * size_t(g.Upts) * tileB * real +        // T ring
                      3 * size_t(g.Upts) * tileB * real +        // W
                      4 * size_t(g.r_cap) * tileB * real +       // A, P, Pg ping-pong
@@ -432,6 +434,7 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->wb.n_rows, sizeof(int) * wt);
   SQ_ALLOC(h->wb.brick_list, sizeof(int) * size_t(wt) * g.nbricks * g.br_cap);
   SQ_ALLOC(h->wb.brick_n, sizeof(int) * size_t(wt) * g.nbricks);
+  SQ_ALLOC(h->wb.brick_rec, sizeof(int4) * 2 * size_t(wt) * g.nbricks * g.br_cap);
   for (int i = 0; i < 3; ++i) SQ_ALLOC(h->wb.T[i], real * size_t(wt) * g.Upts * g.B);
   SQ_ALLOC(h->wb.W, real * size_t(wt) * 3 * g.Upts * g.B);
   SQ_ALLOC(h->wb.A, real * size_t(wt) * g.r_cap * g.B);

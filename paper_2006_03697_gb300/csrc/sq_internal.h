@@ -50,6 +50,12 @@ struct TileEntry {
   int pad;
 };
 
+// An atom image as seen from one 4^3 brick (2 x int4, read warp-uniformly in the sweep):
+//   r0 = {off, row0, ch0, nch | nchp << 8}   off = table index of the brick corner
+//   r1 = {dx, dy, mask_lo, mask_hi}          box extents; 64-bit mask of the brick points
+//                                            (bit a + 4 b + 16 c) inside the support sphere
+// Point (a, b, c) of the brick has its channel group at off + ((c * dy + b) * dx + a) * nchp.
+
 // Everything a tile kernel needs, passed by value.
 struct Geo {
   int n[3];
@@ -89,6 +95,7 @@ struct WaveBufs {
   int* n_rows = nullptr;          // [wt]
   int* brick_list = nullptr;      // [wt][nbricks][br_cap]
   int* brick_n = nullptr;         // [wt][nbricks]
+  int4* brick_rec = nullptr;      // [wt][nbricks][br_cap][2] per-brick image records
   void* T[3] = {nullptr, nullptr, nullptr};   // Real [wt][Upts][B]
   void* W = nullptr;              // Real [wt][3][Upts][B]
   void* A = nullptr;              // Real [wt][r_cap][B]  chi_row(x_q)

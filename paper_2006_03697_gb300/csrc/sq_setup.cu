@@ -95,7 +95,8 @@ __global__ void k_tile_entries(Geo g, Wave w, const AtomTab* __restrict__ atoms,
 // One warp per (brick, tile): entries whose support box meets the brick, in entry order.
 __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ rcmax,
                               const TileEntry* __restrict__ entries, const int* __restrict__ n_entries,
-                              int* __restrict__ blist, int* __restrict__ bn, int* __restrict__ status) {
+                              int* __restrict__ blist, int* __restrict__ bn, int4* __restrict__ rec,
+                              int* __restrict__ status) {
   const int br = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl), lane = threadIdx.x;
   int o[3];
   tile_origin(g, t, o);
@@ -111,9 +112,11 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
   for (int e0 = 0; e0 < ne; e0 += 32) {
     const int e = e0 + lane;
     bool hit = false;
+    TileEntry te;
+    AtomTab at;
     if (e < ne) {
-      const TileEntry te = ent[e];
-      const AtomTab at = atoms[te.atom];
+      te = ent[e];
+      at = atoms[te.atom];
       // the support sphere of the image meets the brick (box test on the lattice, then
       // the distance from the image centre to the brick's bounding box against rcut)
       hit = true;
@@ -130,7 +133,31 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
     }
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
     const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-    if (hit && pos < g.br_cap) out[pos] = e;
+    if (hit && pos < g.br_cap) {
+      out[pos] = e;
+      int l0[3];
+      for (int a = 0; a < 3; ++a) l0[a] = bl[a] - (at.lo[a] + te.s[a] * g.n[a]);
+      const int offc = int(at.off + (long long)((l0[2] * at.dim[1] + l0[1]) * at.dim[0] + l0[0]) * at.nchp);
+      // brick points (a, b, c), bit a + 4 b + 16 c, inside the brick, the box and the support
+      // sphere, with the same arithmetic as the table (a point outside has all channels zero)
+      const double rc = rcmax[te.atom];
+      unsigned long long msk = 0ull;
+      for (int pbit = 0; pbit < 64; ++pbit) {
+        const int pl[3] = {pbit & 3, (pbit >> 2) & 3, pbit >> 4};
+        bool in = true;
+        double r2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const int l = l0[a] + pl[a];
+          in = in && (bl[a] + pl[a] <= bhi[a]) && l >= 0 && l < at.dim[a];
+          const double d = (at.lo[a] + l) * g.h[a] - at.R[a];
+          r2 += d * d;
+        }
+        if (in && r2 <= rc * rc) msk |= 1ull << pbit;
+      }
+      int4* r = rec + (((size_t)tl * g.nbricks + br) * g.br_cap + pos) * 2;
+      r[0] = make_int4(offc, te.row0, at.ch0, at.nch | (at.nchp << 8));
+      r[1] = make_int4(at.dim[0], at.dim[1], int(unsigned(msk & 0xffffffffull)), int(unsigned(msk >> 32)));
+    }
     cnt += __popc(mask);
   }
   if (lane == 0) {
@@ -193,7 +220,7 @@ __global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
     const int pt = (uz * g.U[1] + uy) * g.U[0] + ux;
     int qo[3];
     node_offset(g, q, qo);
-    double acc[3] = {0.0, 0.0, 0.0};
+    Real acc[3] = {Real(0), Real(0), Real(0)};
     if (node_valid(g, o, qo) && in_window(g, qo, ux, uy, uz)) {
       const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
       const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
@@ -206,14 +233,14 @@ __global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
         const int li = box_index(at, te.s, g.n, ax, ay, az);
         if (li < 0) continue;
         const Real* cr = chi_row(chi, at, li);
-        double cs = 0.0;
+        Real cs = Real(0);   // accumulated in the sweep's precision (FP32 suffices for the mixed path)
         for (int c = 0; c < at.nch; ++c)
-          cs += chs[6 * (at.ch0 + c)] * double(At[(size_t)(te.row0 + c) * g.B + q]) * double(cr[c]);
-        if (cs == 0.0) continue;
-        for (int b = 0; b < 3; ++b) acc[b] += cs * (x[b] - (at.R[b] + te.s[b] * g.L[b]));
+          cs += Real(chs[6 * (at.ch0 + c)]) * At[(size_t)(te.row0 + c) * g.B + q] * cr[c];
+        if (cs == Real(0)) continue;
+        for (int b = 0; b < 3; ++b) acc[b] += cs * Real(x[b] - (at.R[b] + te.s[b] * g.L[b]));
       }
     }
-    for (int b = 0; b < 3; ++b) Wt[((size_t)b * g.Upts + pt) * g.B + q] = Real(acc[b]);
+    for (int b = 0; b < 3; ++b) Wt[((size_t)b * g.Upts + pt) * g.B + q] = acc[b];
   }
 }
 
@@ -242,7 +269,7 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, Real* A, R
                                           h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->d.status);
+                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
                                           (Real*)h->wb.Pg[0], (Real*)h->wb.Pg[1]);
@@ -261,7 +288,7 @@ int build_wave_entries(sq_handle* h, const Wave& w) {
   k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows, h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->d.status);
+                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->d.status);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }

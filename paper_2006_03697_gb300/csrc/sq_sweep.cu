@@ -4,14 +4,15 @@
 // and the per-node moments rho^j, K^j_ab, N^j, S^j_ab of each column.
 //
 // Kernels (Real = double for SQ_FP64, float for SQ_MIXED; node sums always FP64):
-//   k_step      one block per (z-slab of 4 planes, tile); one warp = 4 x-adjacent points x the
-//               8 nodes of the tile, so a warp's points share one 4^3 brick and its list of
-//               atom images. Per element: Laplacian + V + nonlocal apply (from Pg^j), the
-//               window mask and the recurrence update; the nonlocal-stress partial
-//               sum_u W_b (grad_a t^j) (the gradient taps reuse the Laplacian loads); and,
-//               fused, the projections gamma |dOmega| chi^T t^{j+1} of the new column
-//               (warp shuffles over the 4 points, shared-memory accumulation per slab,
-//               one global add per row and node).
+//   k_step      one block per (z-slab of 4 planes, tile); each warp walks whole 4^3 bricks,
+//               lanes = 4 x-points x the 8 nodes of the tile, 16 iterations per brick. Per
+//               element: Laplacian + V + nonlocal apply (Pg^j staged in shared memory, only
+//               the atom images whose support sphere holds the point, from a 64-bit mask),
+//               the window mask and the recurrence update, and the nonlocal-stress partial
+//               sum_u W_b (grad_a t^j) (the gradient taps reuse the Laplacian loads). Then,
+//               fused, the projections gamma |dOmega| chi^T t^{j+1} of the new column: summed
+//               over the brick in registers, two warp shuffles, one shared-memory add per
+//               (image, channel, node), one global add per row and node per slab.
 //   k_moments   one block per tile: rho^j, K^j (restricted grad_a grad_b at the node),
 //               N^j = sum_rows chi(x_q) Pg^j, S^j = sum of the slab partials; FP64 table
 //               row; then clears Pg^j, which accumulates the projections of step j + 1.
@@ -145,19 +146,26 @@ __device__ __forceinline__ void load4(const Real* p, Real out[4]) {
 
 constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x 8 nodes
 
-// mode 0: t^1 = Hhat t^0;  mode 1: t^{j+1} = 2 Hhat t^j - t^{j-1};  mode 2: moments only
-template <typename Real, int NO>
+// mode 0: t^1 = Hhat t^0;  mode 1: t^{j+1} = 2 Hhat t^j - t^{j-1};  mode 2: moments only.
+// Each warp walks whole 4^3 bricks of the slab: iteration it covers brick points
+// (a, b, c) = (lane >> 3, it & 3, it >> 2) for node q = lane & 7, so the 4 x-points of an
+// iteration are contiguous in memory and every image record is warp-uniform.
+// kSmemP: stage Pg^j and accumulate the slab's projections in shared memory (false when a
+// tile has too many projector rows; Pg^j is then read and Pg^{j+1} accumulated in global memory)
+template <typename Real, int NO, bool kSmemP>
 __global__ void __launch_bounds__(kThreads)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
        const Real* __restrict__ Pg, Real* __restrict__ Pg_next, const Real* __restrict__ Wt,
-       const Real* __restrict__ chi, const AtomTab* __restrict__ atoms, const Real* __restrict__ gdv,
-       const TileEntry* __restrict__ entries, const int* __restrict__ n_rows, const int* __restrict__ blist,
-       const int* __restrict__ bn, const Real* __restrict__ v, const double* __restrict__ scal, int mode,
-       double* __restrict__ Spart) {
+       const Real* __restrict__ chi, const Real* __restrict__ gdv, const int4* __restrict__ brec,
+       const int* __restrict__ n_rows, const int* __restrict__ bn, const Real* __restrict__ v,
+       const double* __restrict__ scal, int mode, double* __restrict__ Spart, int rows_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* Ps = reinterpret_cast<Real*>(smem_raw);             // [rows][8] projections of this slab
   __shared__ double red[kThreads][9];
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
+  Real* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
+  Real* Ps = kSmemP ? reinterpret_cast<Real*>(smem_raw) : Pn;               // [rows][8] projections
+  const Real* Pgs = kSmemP ? reinterpret_cast<Real*>(smem_raw) + (size_t)rows_smem * kTileB
+                           : Pg + (size_t)tl * g.r_cap * kTileB;           // [rows][8] Pg^j
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int o[3];
   tile_origin(g, t, o);
@@ -167,14 +175,10 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   const size_t tbase = (size_t)tl * g.Upts * kTileB;
   const Real* T = Tc + tbase;
   const Real* Pt = Pg + (size_t)tl * g.r_cap * kTileB;
-  const TileEntry* ent = entries + (size_t)tl * g.e_cap;
   const int nrows = n_rows[tl];
   const bool project = (mode != 2);
-  const int z0 = slab * kBrick, nz = min(kBrick, Uz - z0);
-  const int nel = Ux * Uy * nz * kTileB;                    // multiple of 32 (Ux % 4 == 0)
   const int st[3] = {kTileB, Ux * kTileB, Ux * Uy * kTileB};
   const int Ua[3] = {Ux, Uy, Uz};
-
   Real lap[3][NO + 1], grd[3][NO + 1];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -184,12 +188,16 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
       grd[a][p] = Real(g.grd[a][p]);
     }
   const Real lap0 = Real(g.lap0);
-
-  if (project)
-    for (int i = threadIdx.x; i < nrows * kTileB; i += kThreads) Ps[i] = Real(0);
+  if (kSmemP) {
+    Real* Pstage = const_cast<Real*>(Pgs);
+    for (int i = threadIdx.x; i < nrows * kTileB; i += kThreads) {
+      Pstage[i] = Pt[i];
+      if (project) Ps[i] = Real(0);
+    }
+  }
   __syncthreads();
 
-  const int q = lane & 7;
+  const int q = lane & 7, pa = lane >> 3;
   int qo[3];
   qo[0] = q & 1;
   qo[1] = (q >> 1) & 1;
@@ -200,90 +208,105 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   Real sacc[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) sacc[k] = Real(0);
+  const int nbx = g.nbr[0], nby = g.nbr[1];
 
-  for (int base = warp * 32; base < nel; base += kThreads) {
-    const int i = base + lane;
-    const int p = i >> 3;
-    const int ux = p % Ux, uy = (p / Ux) % Uy, uz = z0 + p / (Ux * Uy);
-    const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + q;
-    const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
-    // the warp's 4 points lie in one brick: its entry list is warp-uniform
-    const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
-    const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
+  for (int bi = warp; bi < nbx * nby; bi += kThreads / 32) {
+    const int bx = bi % nbx, by = bi / nbx;
+    const int br = (slab * nby + by) * nbx + bx;
+    const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
     const int nb = bn[(size_t)tl * g.nbricks + br];
-    const bool inwin = valid && in_window(g, qo, ux, uy, uz);
-    Real tn = Real(0);
-    if (inwin) {
-      const Real tc = T[e];
-      Real y = lap0 * tc;
-      Real gr[3];
-      const int u[3] = {ux, uy, uz};
+    Real tnv[16];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        gr[a] = Real(0);
+    for (int it = 0; it < 16; ++it) {
+      const int pb = it & 3, pc = it >> 2, pbit = pa + 4 * it;
+      const int ux = bx * kBrick + pa, uy = by * kBrick + pb, uz = slab * kBrick + pc;
+      const bool inU = (uy < Uy) && (uz < Uz);
+      const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + q;
+      const bool inwin = inU && valid && in_window(g, qo, ux, uy, uz);
+      Real tn = Real(0);
+      if (inwin) {
+        const Real tc = T[e];
+        Real y = lap0 * tc;
+        Real gr[3];
+        const int u[3] = {ux, uy, uz};
 #pragma unroll
-        for (int pp = 1; pp <= NO; ++pp) {
-          const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
-          const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
-          y += lap[a][pp] * (fp + fm);
-          gr[a] += grd[a][pp] * (fp - fm);
+        for (int a = 0; a < 3; ++a) {
+          gr[a] = Real(0);
+#pragma unroll
+          for (int pp = 1; pp <= NO; ++pp) {
+            const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
+            const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
+            y += lap[a][pp] * (fp + fm);
+            gr[a] += grd[a][pp] * (fp - fm);
+          }
         }
-      }
-      {
-        int wx = ax % g.n[0]; if (wx < 0) wx += g.n[0];
-        int wy = ay % g.n[1]; if (wy < 0) wy += g.n[1];
-        int wz = az % g.n[2]; if (wz < 0) wz += g.n[2];
-        y += v[(wz * g.n[1] + wy) * g.n[0] + wx] * tc;
-      }
-      for (int k = 0; k < nb; ++k) {
-        const TileEntry te = ent[lst[k]];
-        const AtomTab at = atoms[te.atom];
-        const int li = box_index(at, te.s, g.n, ax, ay, az);
-        if (li < 0) continue;
-        const Real* cr = chi_row(chi, at, li);
-        const Real* pr = Pt + (size_t)te.row0 * kTileB + q;
-        for (int c0 = 0; c0 < at.nch; c0 += 4) {
-          Real cv[4];
-          load4(cr + c0, cv);
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (c0 + c < at.nch) y += cv[c] * pr[(c0 + c) * kTileB];
+        {
+          const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
+          int wx = ax % g.n[0]; if (wx < 0) wx += g.n[0];
+          int wy = ay % g.n[1]; if (wy < 0) wy += g.n[1];
+          int wz = az % g.n[2]; if (wz < 0) wz += g.n[2];
+          y += v[(wz * g.n[1] + wy) * g.n[0] + wx] * tc;
         }
-      }
-      if (mode != 2) {
-        const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
-        tn = ca * y + cb * tc - cc * tp;
-        Tn[tbase + e] = tn;
-      }
-      const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
+        for (int k = 0; k < nb; ++k) {
+          const int4 r1 = rb[2 * k + 1];
+          const unsigned mk = (pbit < 32) ? unsigned(r1.z) : unsigned(r1.w);
+          if (!((mk >> (pbit & 31)) & 1u)) continue;
+          const int4 r0 = rb[2 * k];
+          const int nch = r0.w & 0xff, nchp = r0.w >> 8;
+          const Real* cr = chi + r0.x + ((pc * r1.y + pb) * r1.x + pa) * nchp;
+          const Real* pr = Pgs + r0.y * kTileB + q;
+          for (int c0 = 0; c0 < nch; c0 += 4) {
+            Real cv[4];
+            load4(cr + c0, cv);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        sacc[3 * a + 0] += gr[a] * w0;
-        sacc[3 * a + 1] += gr[a] * w1;
-        sacc[3 * a + 2] += gr[a] * w2;
+            for (int c = 0; c < 4; ++c)
+              if (c0 + c < nch) y += cv[c] * pr[(c0 + c) * kTileB];
+          }
+        }
+        if (mode != 2) {
+          const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
+          tn = ca * y + cb * tc - cc * tp;
+          Tn[tbase + e] = tn;
+        }
+        const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          sacc[3 * a + 0] += gr[a] * w0;
+          sacc[3 * a + 1] += gr[a] * w1;
+          sacc[3 * a + 2] += gr[a] * w2;
+        }
+      } else if (inU && mode != 2) {
+        Tn[tbase + e] = Real(0);
       }
-    } else if (mode != 2) {
-      Tn[tbase + e] = Real(0);
+      tnv[it] = tn;
     }
-    // projections of t^{j+1}: gamma |dOmega| chi_row(u) t^{j+1}(u, q), summed over the warp's
-    // 4 points by shuffles, accumulated per slab in shared memory
-    if (project && __any_sync(0xffffffffu, tn != Real(0))) {
+    // projections of t^{j+1} over this brick: each lane sums its 16 points in registers,
+    // two shuffles combine the 4 x-points, lanes 0..7 add one value per node
+    if (project) {
       for (int k = 0; k < nb; ++k) {
-        const TileEntry te = ent[lst[k]];
-        const AtomTab at = atoms[te.atom];
-        const int li = (tn != Real(0)) ? box_index(at, te.s, g.n, ax, ay, az) : -1;
-        if (!__any_sync(0xffffffffu, li >= 0)) continue;
-        for (int c0 = 0; c0 < at.nch; c0 += 4) {
-          Real cv[4] = {Real(0), Real(0), Real(0), Real(0)};
-          if (li >= 0) load4(chi_row(chi, at, li) + c0, cv);
+        const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
+        const int nch = r0.w & 0xff, nchp = r0.w >> 8;
+        for (int c0 = 0; c0 < nch; c0 += 4) {
+          Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+          for (int it = 0; it < 16; ++it) {
+            const int pbit = pa + 4 * it;
+            const unsigned mk = (pbit < 32) ? unsigned(r1.z) : unsigned(r1.w);
+            if (tnv[it] != Real(0) && ((mk >> (pbit & 31)) & 1u)) {
+              Real cv[4];
+              load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[c] += cv[c] * tnv[it];
+            }
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            if (c0 + c < at.nch) {
-              Real s = cv[c] * tn;
+            if (c0 + c < nch) {
+              Real s = acc[c];
               s += __shfl_xor_sync(0xffffffffu, s, 8);
               s += __shfl_xor_sync(0xffffffffu, s, 16);
               if (lane < 8 && s != Real(0))
-                atomicAdd(&Ps[(te.row0 + c0 + c) * kTileB + lane], s * gdv[at.ch0 + c0 + c]);
+                atomicAdd(&Ps[(r0.y + c0 + c) * kTileB + lane], s * gdv[r0.z + c0 + c]);
             }
           }
         }
@@ -300,8 +323,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     for (int th = qq; th < kThreads; th += kTileB) s += red[th][k];
     Spart[(((size_t)tl * g.nslab + slab) * kTileB + qq) * 9 + k] = s;
   }
-  if (project) {
-    Real* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
+  if (kSmemP && project) {
     for (int idx = threadIdx.x; idx < nrows * kTileB; idx += kThreads) {
       const Real s = Ps[idx];
       if (s != Real(0)) atomicAdd(&Pn[idx], s);
@@ -383,11 +405,18 @@ template <typename Real, int NO>
 static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
                        const Real* Pg, Real* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                        int mode) {
-  // the kernel also holds a static [kThreads][9] double array: always opt in to the dynamic size
-  SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  k_step<Real, NO><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.atoms, gdv,
-                                                        h->wb.entries, h->wb.n_rows, h->wb.brick_list, h->wb.brick_n, v,
-                                                        h->d.scal, mode, h->wb.Spart);
+  const int rows_smem = int(smem / (2 * kTileB * sizeof(Real)));
+  if (smem + sizeof(double) * kThreads * 9 <= 200 * 1024) {
+    // the kernel also holds a static [kThreads][9] double array: always opt in to the dynamic size
+    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    k_step<Real, NO, true><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+                                                                h->wb.brick_rec, h->wb.n_rows, h->wb.brick_n, v,
+                                                                h->d.scal, mode, h->wb.Spart, rows_smem);
+  } else {
+    k_step<Real, NO, false><<<grid, kThreads, 0, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+                                                              h->wb.brick_rec, h->wb.n_rows, h->wb.brick_n, v,
+                                                              h->d.scal, mode, h->wb.Spart, 0);
+  }
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }
@@ -423,9 +452,8 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
     SQ_CUDA_TRY(h, cudaMemcpyAsync(nrows.data(), h->wb.n_rows, sizeof(int) * w.ntiles, cudaMemcpyDeviceToHost, s));
     SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
     const int rmax = nrows.empty() ? 0 : *std::max_element(nrows.begin(), nrows.end());
-    const size_t smem = std::max<size_t>(16, size_t(rmax) * kTileB * sizeof(Real));
-    if (smem + sizeof(double) * kThreads * 9 > 220 * 1024)
-      return fail(h, SQ_ERR_INVALID_ARG, "too many projector rows per tile for shared memory");
+    const size_t smem = 2 * std::max<size_t>(1, size_t(rmax)) * kTileB * sizeof(Real);
+
     const dim3 gstencil(g.nslab, w.ntiles);
     // algorithmic bytes of one stencil launch: node columns x region points x vectors moved
     long long nodes = 0;
