@@ -133,7 +133,7 @@ k_apply_h(Geo g, Wave w, const Real* __restrict__ Tc, Real* __restrict__ Tn, con
 // ------------------------------------------------------------------------------ sweep step
 template <typename Real> struct V4;
 template <> struct V4<float> { using T = float4; };
-template <> struct V4<double> { using T = double4; };
+template <> struct V4<double> { using T = double4_32a; };
 
 template <typename Real>
 __device__ __forceinline__ void load4(const Real* p, Real out[4]) {
@@ -153,7 +153,7 @@ constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x
 // kSmemP: stage Pg^j and accumulate the slab's projections in shared memory (false when a
 // tile has too many projector rows; Pg^j is then read and Pg^{j+1} accumulated in global memory)
 template <typename Real, int NO, bool kSmemP>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
        const Real* __restrict__ Pg, Real* __restrict__ Pg_next, const Real* __restrict__ Wt,
        const Real* __restrict__ chi, const Real* __restrict__ gdv, const int4* __restrict__ brec,
@@ -161,6 +161,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
        const double* __restrict__ scal, int mode, double* __restrict__ Spart, int rows_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kThreads][9];
+  __shared__ Real tn_sm[(kThreads / 32) * 16 * 32];
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
   Real* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
   Real* Ps = kSmemP ? reinterpret_cast<Real*>(smem_raw) : Pn;               // [rows][8] projections
@@ -215,8 +216,8 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     const int br = (slab * nby + by) * nbx + bx;
     const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
     const int nb = bn[(size_t)tl * g.nbricks + br];
-    Real tnv[16];
-#pragma unroll
+    Real* tnv = tn_sm + warp * 16 * 32 + lane;   // t^{j+1} of this lane's 16 brick points
+#pragma unroll 1
     for (int it = 0; it < 16; ++it) {
       const int pb = it & 3, pc = it >> 2, pbit = pa + 4 * it;
       const int ux = bx * kBrick + pa, uy = by * kBrick + pb, uz = slab * kBrick + pc;
@@ -278,8 +279,9 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
       } else if (inU && mode != 2) {
         Tn[tbase + e] = Real(0);
       }
-      tnv[it] = tn;
+      tnv[it * 32] = tn;
     }
+    __syncwarp();
     // projections of t^{j+1} over this brick: each lane sums its 16 points in registers,
     // two shuffles combine the 4 x-points, lanes 0..7 add one value per node
     if (project) {
@@ -288,15 +290,16 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
         const int nch = r0.w & 0xff, nchp = r0.w >> 8;
         for (int c0 = 0; c0 < nch; c0 += 4) {
           Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
-#pragma unroll
+#pragma unroll 4
           for (int it = 0; it < 16; ++it) {
             const int pbit = pa + 4 * it;
             const unsigned mk = (pbit < 32) ? unsigned(r1.z) : unsigned(r1.w);
-            if (tnv[it] != Real(0) && ((mk >> (pbit & 31)) & 1u)) {
+            const Real tv = tnv[it * 32];
+            if (tv != Real(0) && ((mk >> (pbit & 31)) & 1u)) {
               Real cv[4];
               load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
 #pragma unroll
-              for (int c = 0; c < 4; ++c) acc[c] += cv[c] * tnv[it];
+              for (int c = 0; c < 4; ++c) acc[c] += cv[c] * tv;
             }
           }
 #pragma unroll
