@@ -191,6 +191,42 @@ int sq_kernel_timing_read(const sq_handle* h, int kid, long long* launches, doub
 int sq_fermi_level_noalloc(const double* mom_dev, int n_nodes, int n_pl, double lambda_lo, double lambda_hi,
                            double kT, double n_e, int cheb_quad_M, void* stream, double* mu_dev);
 
+/* Batched evaluation of independent instances (uneven snapshots): every handle runs its whole
+ * pipeline (sq_moments, sq_fermi_level, contraction at that mu) on its own host thread, at most
+ * max_concurrent (<= 0: n) at a time, so their kernels overlap on the device. Give each handle
+ * its own stream (desc->stream) or they serialise. Outputs (host, may be NULL): mu_out [n],
+ * e_out [n], sigma_out [n][9]. Each result is identical to evaluating that handle alone.
+ * Returns the first non-zero status (details in that handle's sq_last_error). */
+int sq_batch_evaluate(sq_handle* const* hs, int n, int max_concurrent, double* mu_out, sq_energies* e_out,
+                      double* sigma_out);
+
+/* Request loop with continuous batching (one GPU). Requests are admitted in submission order
+ * as soon as their device footprint (sq_footprint_bytes) fits under hbm_budget_bytes next to
+ * those in flight and fewer than max_inflight run; each admitted request runs setup, moments,
+ * Fermi level and contraction on its own stream and host thread and is destroyed afterwards.
+ * A request larger than the whole budget completes with status SQ_ERR_OOM. */
+typedef struct sq_server sq_server;
+typedef struct {
+  long long tag;         /* the caller's tag from sq_server_submit           */
+  int status;            /* SQ_OK or the failing call's status               */
+  double mu;             /* Fermi level (Ha)                                  */
+  sq_energies energies;  /* as sq_density_energy_stress                       */
+  double sigma[9];       /* Ha/bohr^3, row-major                             */
+  double latency_ms;     /* submit -> result available                       */
+} sq_result;
+int sq_server_create(size_t hbm_budget_bytes, int max_inflight, sq_server** out);
+/* Copies every input of desc (desc->stream is ignored); returns SQ_ERR_INVALID_ARG if desc
+ * does not validate, SQ_ERR_STATE after sq_server_destroy has begun. Non-blocking. */
+int sq_server_submit(sq_server* s, const sq_instance_desc* desc, long long tag);
+/* Moves up to max_results finished results to out (host), waiting up to timeout_ms for the
+ * first one; *n_out receives the count. */
+int sq_server_poll(sq_server* s, sq_result* out, int max_results, int timeout_ms, int* n_out);
+/* Requests queued or running (-1 for NULL). */
+int sq_server_pending(sq_server* s);
+/* Stops admitting, finishes every queued and running request, frees the server (results not
+ * polled are dropped). */
+void sq_server_destroy(sq_server* s);
+
 void sq_destroy(sq_handle* h);
 
 /* Last error text of h (or of the last failed sq_setup when h is NULL); never NULL. */

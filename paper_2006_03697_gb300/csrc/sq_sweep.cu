@@ -153,14 +153,14 @@ constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x
 // kSmemP: stage Pg^j and accumulate the slab's projections in shared memory (false when a
 // tile has too many projector rows; Pg^j is then read and Pg^{j+1} accumulated in global memory)
 template <typename Real, int NO, bool kSmemP>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
        const Real* __restrict__ Pg, Real* __restrict__ Pg_next, const Real* __restrict__ Wt,
        const Real* __restrict__ chi, const Real* __restrict__ gdv, const int4* __restrict__ brec,
        const int* __restrict__ n_rows, const int* __restrict__ bn, const Real* __restrict__ v,
        const double* __restrict__ scal, int mode, double* __restrict__ Spart, int rows_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[kThreads][9];
+  __shared__ double red[kThreads / 32][kTileB][9];
   __shared__ Real tn_sm[(kThreads / 32) * 16 * 32];
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
   Real* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
@@ -216,16 +216,47 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     const int br = (slab * nby + by) * nbx + bx;
     const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
     const int nb = bn[(size_t)tl * g.nbricks + br];
-    Real* tnv = tn_sm + warp * 16 * 32 + lane;   // t^{j+1} of this lane's 16 brick points
+    Real* tnv = tn_sm + warp * 16 * 32 + lane;   // per lane and brick point: V_nl t^j, then t^{j+1}
+    // phase A: nonlocal apply, record-major: sum_rows chi_row(u) Pg^j[row][q] for the lane's
+    // 16 points; the table loads of one record are independent of each other
+    {
+      Real ynl[16];
+#pragma unroll
+      for (int it = 0; it < 16; ++it) ynl[it] = Real(0);
+      for (int k = 0; k < nb; ++k) {
+        const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
+        const int nch = r0.w & 0xff, nchp = r0.w >> 8;
+        const unsigned long long mk64 = (unsigned long long)(unsigned)r1.z | ((unsigned long long)(unsigned)r1.w << 32);
+        for (int c0 = 0; c0 < nch; c0 += 4) {
+          Real pv[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) pv[c] = (c0 + c < nch) ? Pgs[(r0.y + c0 + c) * kTileB + q] : Real(0);
+#pragma unroll
+          for (int it = 0; it < 16; ++it) {
+            if ((mk64 >> (pa + 4 * it)) & 1ull) {
+              Real cv[4];
+              load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
+              ynl[it] += cv[0] * pv[0] + cv[1] * pv[1] + cv[2] * pv[2] + cv[3] * pv[3];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < 16; ++it) tnv[it * 32] = ynl[it];
+    }
+    __syncwarp();
 #pragma unroll 1
     for (int it = 0; it < 16; ++it) {
-      const int pb = it & 3, pc = it >> 2, pbit = pa + 4 * it;
+      const int pb = it & 3, pc = it >> 2;
       const int ux = bx * kBrick + pa, uy = by * kBrick + pb, uz = slab * kBrick + pc;
       const bool inU = (uy < Uy) && (uz < Uz);
       const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + q;
       const bool inwin = inU && valid && in_window(g, qo, ux, uy, uz);
       Real tn = Real(0);
       if (inwin) {
+        // loads that do not depend on the stencil, issued first
+        const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
+        const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
         const Real tc = T[e];
         Real y = lap0 * tc;
         Real gr[3];
@@ -248,28 +279,11 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
           int wz = az % g.n[2]; if (wz < 0) wz += g.n[2];
           y += v[(wz * g.n[1] + wy) * g.n[0] + wx] * tc;
         }
-        for (int k = 0; k < nb; ++k) {
-          const int4 r1 = rb[2 * k + 1];
-          const unsigned mk = (pbit < 32) ? unsigned(r1.z) : unsigned(r1.w);
-          if (!((mk >> (pbit & 31)) & 1u)) continue;
-          const int4 r0 = rb[2 * k];
-          const int nch = r0.w & 0xff, nchp = r0.w >> 8;
-          const Real* cr = chi + r0.x + ((pc * r1.y + pb) * r1.x + pa) * nchp;
-          const Real* pr = Pgs + r0.y * kTileB + q;
-          for (int c0 = 0; c0 < nch; c0 += 4) {
-            Real cv[4];
-            load4(cr + c0, cv);
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (c0 + c < nch) y += cv[c] * pr[(c0 + c) * kTileB];
-          }
-        }
+        y += tnv[it * 32];                          // nonlocal part from phase A
         if (mode != 2) {
-          const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
           tn = ca * y + cb * tc - cc * tp;
           Tn[tbase + e] = tn;
         }
-        const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           sacc[3 * a + 0] += gr[a] * w0;
@@ -316,15 +330,20 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
       }
     }
   }
-  // S partials: fixed-order block reduction per node
+  // S partials: fixed-order reduction per node (the 4 point lanes by shuffles, then warps)
 #pragma unroll
-  for (int k = 0; k < 9; ++k) red[threadIdx.x][k] = double(sacc[k]);
+  for (int k = 0; k < 9; ++k) {
+    double sv = double(sacc[k]);
+    sv += __shfl_xor_sync(0xffffffffu, sv, 8);
+    sv += __shfl_xor_sync(0xffffffffu, sv, 16);
+    if (lane < kTileB) red[warp][lane][k] = sv;
+  }
   __syncthreads();
   for (int k2 = threadIdx.x; k2 < kTileB * 9; k2 += kThreads) {
     const int qq = k2 / 9, k = k2 % 9;
-    double s = 0.0;
-    for (int th = qq; th < kThreads; th += kTileB) s += red[th][k];
-    Spart[(((size_t)tl * g.nslab + slab) * kTileB + qq) * 9 + k] = s;
+    double sv = 0.0;
+    for (int wv = 0; wv < kThreads / 32; ++wv) sv += red[wv][qq][k];
+    Spart[(((size_t)tl * g.nslab + slab) * kTileB + qq) * 9 + k] = sv;
   }
   if (kSmemP && project) {
     for (int idx = threadIdx.x; idx < nrows * kTileB; idx += kThreads) {
@@ -409,8 +428,8 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
                        const Real* Pg, Real* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                        int mode) {
   const int rows_smem = int(smem / (2 * kTileB * sizeof(Real)));
-  if (smem + sizeof(double) * kThreads * 9 <= 200 * 1024) {
-    // the kernel also holds a static [kThreads][9] double array: always opt in to the dynamic size
+  if (smem <= 160 * 1024) {
+    // the kernel also holds static shared arrays: always opt in to the dynamic size
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     k_step<Real, NO, true><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
                                                                 h->wb.brick_rec, h->wb.n_rows, h->wb.brick_n, v,

@@ -29,7 +29,8 @@ SQ_N_MOMENTS = 17
 EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
-    "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_destroy", "sq_last_error",
+    "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit",
+    "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_destroy", "sq_last_error",
 ]
 SQ_K_STENCIL = 0
 SQ_K_PROJECT = 1
@@ -56,6 +57,11 @@ class sq_instance_desc(C.Structure):
 class sq_energies(C.Structure):
     _fields_ = [("E_band", C.c_double), ("E_s", C.c_double), ("E_nl", C.c_double),
                 ("F", C.c_double), ("N_check", C.c_double), ("mu", C.c_double)]
+
+
+class sq_result(C.Structure):
+    _fields_ = [("tag", C.c_longlong), ("status", C.c_int), ("mu", C.c_double), ("energies", sq_energies),
+                ("sigma", C.c_double * 9), ("latency_ms", C.c_double)]
 
 
 class SQError(RuntimeError):
@@ -94,6 +100,18 @@ def lib():
         L.sq_fermi_level_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                              C.c_double, C.c_int, C.c_void_p, C.c_void_p]
         L.sq_fermi_level_noalloc.restype = C.c_int
+        L.sq_batch_evaluate.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.sq_batch_evaluate.restype = C.c_int
+        L.sq_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]
+        L.sq_server_create.restype = C.c_int
+        L.sq_server_submit.argtypes = [C.c_void_p, C.POINTER(sq_instance_desc), C.c_longlong]
+        L.sq_server_submit.restype = C.c_int
+        L.sq_server_poll.argtypes = [C.c_void_p, C.POINTER(sq_result), C.c_int, C.c_int, C.POINTER(C.c_int)]
+        L.sq_server_poll.restype = C.c_int
+        L.sq_server_pending.argtypes = [C.c_void_p]
+        L.sq_server_pending.restype = C.c_int
+        L.sq_server_destroy.argtypes = [C.c_void_p]
+        L.sq_server_destroy.restype = None
         L.sq_destroy.argtypes = [H]
         L.sq_destroy.restype = None
         L.sq_last_error.argtypes = [H]
@@ -256,3 +274,50 @@ def run(inst: dict, precision=SQ_FP64, bounds=None, want_moments=False, stream=N
         return out
     finally:
         sq_destroy(h)
+
+
+def sq_batch_evaluate(handles, max_concurrent: int = 0):
+    """Evaluates every handle concurrently; returns (mu (n,), energies list, sigma (n, 3, 3))."""
+    n = len(handles)
+    arr = (C.c_void_p * max(1, n))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    mu = np.zeros(n)
+    en = (sq_energies * max(1, n))()
+    sig = np.zeros((n, 9))
+    rc = lib().sq_batch_evaluate(arr, n, max_concurrent, mu.ctypes.data, C.cast(en, C.c_void_p), sig.ctypes.data)
+    if rc != SQ_OK:
+        raise SQError(rc, "sq_batch_evaluate failed (see the handles' sq_last_error)")
+    energies = [{k: getattr(en[i], k) for k, _ in sq_energies._fields_} for i in range(n)]
+    return mu, energies, sig.reshape(n, 3, 3)
+
+
+class Server:
+    """sq_server_* request loop (argument marshalling only)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int):
+        self.h = C.c_void_p()
+        _check(lib().sq_server_create(int(hbm_budget_bytes), int(max_inflight), C.byref(self.h)))
+
+    def submit(self, desc: Desc, tag: int):
+        rc = lib().sq_server_submit(self.h, C.byref(desc.c), int(tag))
+        if rc != SQ_OK:
+            raise SQError(rc, "sq_server_submit rejected the request")
+
+    def poll(self, max_results: int = 64, timeout_ms: int = 100):
+        buf = (sq_result * max_results)()
+        n = C.c_int()
+        _check(lib().sq_server_poll(self.h, buf, max_results, timeout_ms, C.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            out.append({"tag": r.tag, "status": r.status, "mu": r.mu, "latency_ms": r.latency_ms,
+                        "sigma": np.array(list(r.sigma)).reshape(3, 3),
+                        **{k: getattr(r.energies, k) for k, _ in sq_energies._fields_}})
+        return out
+
+    def pending(self) -> int:
+        return int(lib().sq_server_pending(self.h))
+
+    def close(self):
+        if self.h:
+            lib().sq_server_destroy(self.h)
+            self.h = C.c_void_p()

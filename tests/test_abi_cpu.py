@@ -69,3 +69,32 @@ def test_null_handle_calls_are_rejected(sq):
     assert L.sq_fermi_level(None, None) == sq.SQ_ERR_INVALID_ARG
     assert L.sq_kernel_launches(None) == 0
     L.sq_destroy(None)
+
+
+def test_server_refuses_request_larger_than_budget(sq):
+    """Admission by device footprint: a request that can never fit completes with SQ_ERR_OOM
+    without touching a GPU."""
+    srv = sq.Server(hbm_budget_bytes=1024, max_inflight=2)
+    try:
+        d = sq.Desc(tiny_instance(seed=0), sq.SQ_FP64, bounds=(-1.0, 20.0))
+        srv.submit(d, tag=7)
+        got = []
+        for _ in range(50):
+            got += srv.poll(timeout_ms=100)
+            if got:
+                break
+        assert len(got) == 1 and got[0]["tag"] == 7 and got[0]["status"] == sq.SQ_ERR_OOM
+        assert srv.pending() == 0
+    finally:
+        srv.close()
+
+
+def test_server_rejects_invalid_descriptor(sq):
+    srv = sq.Server(hbm_budget_bytes=1 << 30, max_inflight=1)
+    try:
+        d = sq.Desc(tiny_instance(seed=0), sq.SQ_FP64, bounds=(-1.0, 20.0))
+        d.c.n_o = 0
+        with pytest.raises(sq.SQError):
+            srv.submit(d, tag=1)
+    finally:
+        srv.close()
