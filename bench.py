@@ -195,7 +195,8 @@ def serve_stream(sq, n_req: int, prec: int):
     finally:
         srv.close()
     lat = np.sort(np.array([r["latency_ms"] for r in got]))
-    return {"requests": n_req, "ok": all(r["status"] == 0 for r in got), "evals_per_s": n_req / wall,
+    return {"requests": n_req, "ok": all(r["status"] == 0 for r in got),
+            "failed_statuses": sorted(int(r["status"]) for r in got if r["status"] != 0), "evals_per_s": n_req / wall,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "alone_ms": t_one * 1000.0, "arrival_rate_per_s": 1.5 / t_one, "max_inflight": 4,
             "workload": "32-atom snapshots of the batched config (9.6 bohr cube, 32^3 nodes, kT in "
