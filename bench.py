@@ -196,7 +196,7 @@ def serve_stream(sq, n_req: int, prec: int):
         srv.close()
     lat = np.sort(np.array([r["latency_ms"] for r in got]))
     return {"requests": n_req, "ok": all(r["status"] == 0 for r in got),
-            "failed_statuses": sorted(int(r["status"]) for r in got if r["status"] != 0), "evals_per_s": n_req / wall,
+            "failed": [(int(r["status"]), r["error"]) for r in got if r["status"] != 0], "evals_per_s": n_req / wall,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "alone_ms": t_one * 1000.0, "arrival_rate_per_s": 1.5 / t_one, "max_inflight": 4,
             "workload": "32-atom snapshots of the batched config (9.6 bohr cube, 32^3 nodes, kT in "
@@ -229,6 +229,21 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The slowest rank's value (max-reduction); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, max_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak scaling)."""
+    return world * units_per_rank / (max_ms / 1000.0)
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -291,12 +306,9 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1000.0)
+    value = whole_job_rate(world, args.steps, ms)
 
     # e2e: the public C ABI from host buffers, setup copies and host outputs inside the region
     rho_h = np.zeros(nd)
@@ -314,10 +326,7 @@ def run_ours(args):
         sq.sq_destroy(hh)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     e2e = {"value": world * args.steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h)}
 

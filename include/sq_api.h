@@ -213,6 +213,7 @@ typedef struct {
   sq_energies energies;  /* as sq_density_energy_stress                       */
   double sigma[9];       /* Ha/bohr^3, row-major                             */
   double latency_ms;     /* submit -> result available                       */
+  char error[128];       /* sq_last_error text when status != SQ_OK          */
 } sq_result;
 int sq_server_create(size_t hbm_budget_bytes, int max_inflight, sq_server** out);
 /* Copies every input of desc (desc->stream is ignored); returns SQ_ERR_INVALID_ARG if desc

@@ -151,6 +151,12 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
       }
     g.lap0 = double(float(-side));
   }
+  g.lap0f = float(g.lap0);
+  for (int a = 0; a < 3; ++a)
+    for (int p = 0; p <= sq::kMaxNo; ++p) {
+      g.lapf[a][p] = float(g.lap[a][p]);
+      g.grdf[a][p] = float(g.grd[a][p]);
+    }
   // atoms: base image wrapped into the cell, support box of the largest projector radius
   P.atoms.clear();
   long long off = 0;
@@ -220,8 +226,10 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
                      size_t(g.nbricks) * size_t(g.br_cap) * 2 * sizeof(int4) +
                      3 * size_t(g.Upts) * tileB * real +        // T ring
                      3 * size_t(g.Upts) * tileB * real +        // W
-                     4 * size_t(g.r_cap) * tileB * real +       // A, P, Pg ping-pong
-                     size_t(g.nslab) * tileB * 9 * sizeof(double);
+                     2 * size_t(g.r_cap) * tileB * real +       // A, P
+                     2 * size_t(g.r_cap) * tileB * sizeof(double) +   // Pg ping-pong (FP64)
+                     size_t(g.nslab) * tileB * 9 * sizeof(double) +
+                     size_t(g.nslab) * (size_t(g.r_cap) + 1) * sizeof(int);   // slab row maps
   long long Nd = (long long)g.n[0] * g.n[1] * g.n[2];
   int M = d->cheb_quad_M > 0 ? d->cheb_quad_M : 2048;
   P.fixed_bytes = size_t(Nd) * (sizeof(double) + sizeof(float)) +                       // V
@@ -283,17 +291,25 @@ int set_bounds(sq_handle* h, double lo, double hi) {
     cb = double(float(-2.0 * chi / zeta));
     chi = -cb * zeta / 2.0;
   }
-  // the stored stencil adds lap_offset * t: the recurrence runs on (H + offset - chi) / zeta
-  chi -= h->lap_offset;
+  // The sweep multiplies t by one diagonal coefficient cd = ca lap0 + cb (plus ca V), formed
+  // here in FP64 so the large, nearly cancelling diagonal terms never meet in FP32; its
+  // rounding eps to the sweep precision acts as a constant shift eps / ca of the operator.
+  double cd = ca * h->geo.lap0 + cb;
+  if (h->precision == SQ_MIXED) cd = double(float(cd));
+  const double eps = cd - (ca * h->geo.lap0 + cb);
+  // the stored stencil adds (lap_offset + eps / ca) t: the recurrence runs on
+  // (H + offset - chi) / zeta, so the effective centre moves down by that offset
+  chi -= h->lap_offset + eps / ca;
   h->lam_lo = chi - zeta;
   h->lam_hi = chi + zeta;
   h->hscal[0] = h->lam_lo;
   h->hscal[1] = h->lam_hi;
   h->hscal[2] = ca;
   h->hscal[3] = cb;
+  h->hscal[4] = cd;
   cudaError_t e = cudaMemcpyAsync(h->d.scal, h->hscal, 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->d.scal + 4, h->hscal + 2, 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(h->d.scal + 4, h->hscal + 2, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return fail(h, SQ_ERR_CUDA, std::string("set_bounds: ") + cudaGetErrorString(e));
   return SQ_OK;
 }
@@ -435,12 +451,14 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->wb.brick_list, sizeof(int) * size_t(wt) * g.nbricks * g.br_cap);
   SQ_ALLOC(h->wb.brick_n, sizeof(int) * size_t(wt) * g.nbricks);
   SQ_ALLOC(h->wb.brick_rec, sizeof(int4) * 2 * size_t(wt) * g.nbricks * g.br_cap);
+  SQ_ALLOC(h->wb.slab_n, sizeof(int) * size_t(wt) * g.nslab);
+  SQ_ALLOC(h->wb.slab_map, sizeof(int) * size_t(wt) * g.nslab * g.r_cap);
   for (int i = 0; i < 3; ++i) SQ_ALLOC(h->wb.T[i], real * size_t(wt) * g.Upts * g.B);
   SQ_ALLOC(h->wb.W, real * size_t(wt) * 3 * g.Upts * g.B);
   SQ_ALLOC(h->wb.A, real * size_t(wt) * g.r_cap * g.B);
   SQ_ALLOC(h->wb.P, real * size_t(wt) * g.r_cap * g.B);
-  SQ_ALLOC(h->wb.Pg[0], real * size_t(wt) * g.r_cap * g.B);
-  SQ_ALLOC(h->wb.Pg[1], real * size_t(wt) * g.r_cap * g.B);
+  SQ_ALLOC(h->wb.Pg[0], sizeof(double) * size_t(wt) * g.r_cap * g.B);   // projections: FP64 sums
+  SQ_ALLOC(h->wb.Pg[1], sizeof(double) * size_t(wt) * g.r_cap * g.B);
   SQ_ALLOC(h->wb.Spart, sizeof(double) * size_t(wt) * g.nslab * g.B * 9);
   if (!h->lanczos_tiles.empty()) {
     const size_t nst = h->lanczos_tiles.size();

@@ -31,6 +31,7 @@ constexpr int kMaxNo = 6;        // largest FD half-order supported
 constexpr int kBrick = 4;        // brick side in points
 constexpr int kMaxCh = 8;        // projector channels per atom
 constexpr int kThreads = 256;    // block size of the tile kernels
+constexpr int kMaxU = 2 * 64 + 8; // largest union-window extent (m <= 64, b = 2, x padded to 4)
 
 struct AtomTab {
   int lo[3];        // support box corner (absolute lattice coordinates of the base image)
@@ -75,6 +76,9 @@ struct Geo {
   double lap0;                    // -1/2 sum_a w0 / h_a^2
   double lap[3][kMaxNo + 1];      // -1/2 w_p / h_a^2
   double grd[3][kMaxNo + 1];      // g_p / h_a
+  float lap0f;                    // float copies used by the FP32 sweep (constant-bank operands)
+  float lapf[3][kMaxNo + 1];
+  float grdf[3][kMaxNo + 1];
   int e_cap;                      // entries per tile (capacity)
   int r_cap;                      // projector rows per tile (capacity)
   int br_cap;                     // entries per brick (capacity)
@@ -96,11 +100,13 @@ struct WaveBufs {
   int* brick_list = nullptr;      // [wt][nbricks][br_cap]
   int* brick_n = nullptr;         // [wt][nbricks]
   int4* brick_rec = nullptr;      // [wt][nbricks][br_cap][2] per-brick image records
+  int* slab_n = nullptr;          // [wt][nslab] projector rows meeting each z-slab
+  int* slab_map = nullptr;        // [wt][nslab][r_cap] slab row -> tile row
   void* T[3] = {nullptr, nullptr, nullptr};   // Real [wt][Upts][B]
   void* W = nullptr;              // Real [wt][3][Upts][B]
   void* A = nullptr;              // Real [wt][r_cap][B]  chi_row(x_q)
   void* P = nullptr;              // Real [wt][r_cap][B]  gamma |dOmega| chi^T t (Lanczos apply)
-  void* Pg[2] = {nullptr, nullptr};   // Real [wt][r_cap][B]  gamma |dOmega| chi^T t^j, ping-pong
+  void* Pg[2] = {nullptr, nullptr};   // double [wt][r_cap][B]  gamma |dOmega| chi^T t^j, ping-pong
   double* Spart = nullptr;        // [wt][nslab][B][9]
 };
 

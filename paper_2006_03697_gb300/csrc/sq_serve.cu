@@ -65,6 +65,7 @@ void run_request(sq_server* s, Request* rq) {
   if (rc == SQ_OK) rc = sq_moments(h);
   if (rc == SQ_OK) rc = sq_fermi_level(h, &res.mu);
   if (rc == SQ_OK) rc = sq_density_energy_stress(h, res.mu, nullptr, &res.energies, res.sigma);
+  if (rc != SQ_OK) std::strncpy(res.error, sq_last_error(h), sizeof(res.error) - 1);
   if (h) sq_destroy(h);
   if (st) cudaStreamDestroy(st);
   res.status = rc;
@@ -99,6 +100,7 @@ void dispatch_loop(sq_server* s) {
       std::memset(&res, 0, sizeof(res));
       res.tag = rq->tag;
       res.status = SQ_ERR_OOM;
+      std::strncpy(res.error, "device footprint exceeds the server's budget", sizeof(res.error) - 1);
       res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - rq->t_submit).count();
       s->results.push_back(res);
       delete rq;

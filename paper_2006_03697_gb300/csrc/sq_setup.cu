@@ -92,11 +92,32 @@ __global__ void k_tile_entries(Geo g, Wave w, const AtomTab* __restrict__ atoms,
   }
 }
 
-// One warp per (brick, tile): entries whose support box meets the brick, in entry order.
+// Support sphere of an atom image against a lattice box [bl, bhi] (absolute coords): the
+// table box overlaps it and the distance from the image centre to its bounding box is <= rcut.
+__device__ __forceinline__ bool image_meets_box(const Geo& g, const TileEntry& te, const AtomTab& at, double rc,
+                                                const int bl[3], const int bhi[3]) {
+  bool hit = true;
+  double d2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const int lo = at.lo[a] + te.s[a] * g.n[a], hi = lo + at.dim[a] - 1;
+    hit = hit && (lo <= bhi[a]) && (hi >= bl[a]);
+    const double c = at.R[a] + te.s[a] * g.L[a];
+    const double blo = bl[a] * g.h[a], bhi_x = bhi[a] * g.h[a];
+    const double dd = (c < blo) ? blo - c : (c > bhi_x ? c - bhi_x : 0.0);
+    d2 += dd * dd;
+  }
+  return hit && (d2 <= rc * rc * (1.0 + 1e-12) + 1e-24);
+}
+
+// One warp per (brick, tile): entries whose support sphere meets the brick, in entry order,
+// and their records. The projector rows of the entries that meet the brick's z-slab (a
+// superset of its bricks' entries: the slab's bounding box contains each brick's) are
+// numbered slab-locally in entry order; the record carries that number (bits 16..31 of r0.w)
+// and the first brick of the slab writes the slab's row map (slab row -> tile row) and count.
 __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ rcmax,
                               const TileEntry* __restrict__ entries, const int* __restrict__ n_entries,
                               int* __restrict__ blist, int* __restrict__ bn, int4* __restrict__ rec,
-                              int* __restrict__ status) {
+                              int* __restrict__ slab_n, int* __restrict__ slab_map, int* __restrict__ status) {
   const int br = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl), lane = threadIdx.x;
   int o[3];
   tile_origin(g, t, o);
@@ -105,64 +126,83 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
   const int bhi[3] = {o[0] - g.m[0] + min(g.U[0], (bx + 1) * kBrick) - 1,
                       o[1] - g.m[1] + min(g.U[1], (by + 1) * kBrick) - 1,
                       o[2] - g.m[2] + min(g.U[2], (bz + 1) * kBrick) - 1};
+  // the slab: all of U in x and y, the brick's planes in z
+  const int sl[3] = {o[0] - g.m[0], o[1] - g.m[1], bl[2]};
+  const int shi[3] = {o[0] - g.m[0] + g.U[0] - 1, o[1] - g.m[1] + g.U[1] - 1, bhi[2]};
+  const bool slab_writer = (bx == 0 && by == 0);
+  int* smap = slab_map + ((size_t)tl * g.nslab + bz) * g.r_cap;
   const int ne = n_entries[tl];
   const TileEntry* ent = entries + (size_t)tl * g.e_cap;
   int* out = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
-  int cnt = 0;
+  int cnt = 0, srow_base = 0;
   for (int e0 = 0; e0 < ne; e0 += 32) {
     const int e = e0 + lane;
     bool hit = false;
+    int nch_slab = 0;
     TileEntry te;
     AtomTab at;
     if (e < ne) {
       te = ent[e];
       at = atoms[te.atom];
-      // the support sphere of the image meets the brick (box test on the lattice, then
-      // the distance from the image centre to the brick's bounding box against rcut)
-      hit = true;
-      double d2 = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        const int lo = at.lo[a] + te.s[a] * g.n[a], hi = lo + at.dim[a] - 1;
-        hit = hit && (lo <= bhi[a]) && (hi >= bl[a]);
-        const double c = at.R[a] + te.s[a] * g.L[a];
-        const double blo = bl[a] * g.h[a], bhi_x = bhi[a] * g.h[a];
-        const double dd = (c < blo) ? blo - c : (c > bhi_x ? c - bhi_x : 0.0);
-        d2 += dd * dd;
-      }
-      hit = hit && (d2 <= rcmax[te.atom] * rcmax[te.atom] * (1.0 + 1e-12) + 1e-24);
+      hit = image_meets_box(g, te, at, rcmax[te.atom], bl, bhi);
+      if (image_meets_box(g, te, at, rcmax[te.atom], sl, shi)) nch_slab = at.nch;
     }
+    // slab-local first row of the lane's entry: exclusive warp scan of the slab entries' rows
+    int incl = nch_slab;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int srow = srow_base + incl - nch_slab;
+    if (slab_writer)
+      for (int c = 0; c < nch_slab; ++c) smap[srow + c] = te.row0 + c;
+    srow_base += __shfl_sync(0xffffffffu, incl, 31);
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
     const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-    if (hit && pos < g.br_cap) {
-      out[pos] = e;
+    if (hit && pos < g.br_cap) out[pos] = e;
+    // one record per hit image, built by the whole warp: lane L tests brick points L and L + 32
+    // (bit a + 4 b + 16 c) for lying in the brick, the box and the support sphere, with the same
+    // arithmetic as the table (a point outside has all channels zero)
+    for (unsigned hm = mask; hm; hm &= hm - 1u) {
+      const int src = __ffs(hm) - 1;
+      const int pos_s = cnt + __popc(mask & ((1u << src) - 1u));
+      const int e_s = e0 + src;
+      if (pos_s >= g.br_cap) break;
+      const TileEntry tes = ent[e_s];
+      const AtomTab ats = atoms[tes.atom];
+      const int srow_s = __shfl_sync(0xffffffffu, srow, src);
       int l0[3];
-      for (int a = 0; a < 3; ++a) l0[a] = bl[a] - (at.lo[a] + te.s[a] * g.n[a]);
-      const int offc = int(at.off + (long long)((l0[2] * at.dim[1] + l0[1]) * at.dim[0] + l0[0]) * at.nchp);
-      // brick points (a, b, c), bit a + 4 b + 16 c, inside the brick, the box and the support
-      // sphere, with the same arithmetic as the table (a point outside has all channels zero)
-      const double rc = rcmax[te.atom];
-      unsigned long long msk = 0ull;
-      for (int pbit = 0; pbit < 64; ++pbit) {
+      for (int a = 0; a < 3; ++a) l0[a] = bl[a] - (ats.lo[a] + tes.s[a] * g.n[a]);
+      const double rc = rcmax[tes.atom];
+      bool inpt[2];
+      for (int hh = 0; hh < 2; ++hh) {
+        const int pbit = lane + 32 * hh;
         const int pl[3] = {pbit & 3, (pbit >> 2) & 3, pbit >> 4};
         bool in = true;
         double r2 = 0.0;
         for (int a = 0; a < 3; ++a) {
           const int l = l0[a] + pl[a];
-          in = in && (bl[a] + pl[a] <= bhi[a]) && l >= 0 && l < at.dim[a];
-          const double d = (at.lo[a] + l) * g.h[a] - at.R[a];
+          in = in && (bl[a] + pl[a] <= bhi[a]) && l >= 0 && l < ats.dim[a];
+          const double d = (ats.lo[a] + l) * g.h[a] - ats.R[a];
           r2 += d * d;
         }
-        if (in && r2 <= rc * rc) msk |= 1ull << pbit;
+        inpt[hh] = in && r2 <= rc * rc;
       }
-      int4* r = rec + (((size_t)tl * g.nbricks + br) * g.br_cap + pos) * 2;
-      r[0] = make_int4(offc, te.row0, at.ch0, at.nch | (at.nchp << 8));
-      r[1] = make_int4(at.dim[0], at.dim[1], int(unsigned(msk & 0xffffffffull)), int(unsigned(msk >> 32)));
+      const unsigned lo32 = __ballot_sync(0xffffffffu, inpt[0]);
+      const unsigned hi32 = __ballot_sync(0xffffffffu, inpt[1]);
+      if (lane == 0) {
+        const int offc = int(ats.off + (long long)((l0[2] * ats.dim[1] + l0[1]) * ats.dim[0] + l0[0]) * ats.nchp);
+        int4* r = rec + (((size_t)tl * g.nbricks + br) * g.br_cap + pos_s) * 2;
+        r[0] = make_int4(offc, tes.row0, ats.ch0, ats.nch | (ats.nchp << 8) | (min(srow_s, 0xffff) << 16));
+        r[1] = make_int4(ats.dim[0], ats.dim[1], int(lo32), int(hi32));
+      }
     }
     cnt += __popc(mask);
   }
   if (lane == 0) {
     bn[(size_t)tl * g.nbricks + br] = min(cnt, g.br_cap);
     if (cnt > g.br_cap) atomicOr(status + kStOverflow, 2);
+    if (slab_writer) slab_n[(size_t)tl * g.nslab + bz] = srow_base;
   }
 }
 
@@ -171,16 +211,16 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
 template <typename Real>
 __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ chs,
                          const Real* __restrict__ chi, const TileEntry* __restrict__ entries,
-                         const int* __restrict__ n_entries, Real* __restrict__ A, Real* __restrict__ Pg0_,
-                         Real* __restrict__ Pg1_) {
+                         const int* __restrict__ n_entries, Real* __restrict__ A, double* __restrict__ Pg0_,
+                         double* __restrict__ Pg1_) {
   const int tl = blockIdx.x, t = wave_tile(w, tl);
   int o[3];
   tile_origin(g, t, o);
   const int ne = n_entries[tl];
   const TileEntry* ent = entries + (size_t)tl * g.e_cap;
   Real* At = A + (size_t)tl * g.r_cap * g.B;
-  Real* Pg0 = Pg0_ + (size_t)tl * g.r_cap * g.B;
-  Real* Pg1 = Pg1_ + (size_t)tl * g.r_cap * g.B;
+  double* Pg0 = Pg0_ + (size_t)tl * g.r_cap * g.B;
+  double* Pg1 = Pg1_ + (size_t)tl * g.r_cap * g.B;
   for (int i = threadIdx.x; i < ne * g.B; i += blockDim.x) {
     const int e = i / g.B, q = i % g.B;
     const TileEntry te = ent[e];
@@ -193,8 +233,8 @@ __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
     for (int c = 0; c < at.nch; ++c) {
       const double x = (li >= 0) ? double(chi_row(chi, at, li)[c]) : 0.0;
       At[(size_t)(te.row0 + c) * g.B + q] = Real(x);
-      Pg0[(size_t)(te.row0 + c) * g.B + q] = Real(chs[6 * (at.ch0 + c)] * x);   // gamma |dOmega| chi^T t^0
-      Pg1[(size_t)(te.row0 + c) * g.B + q] = Real(0);
+      Pg0[(size_t)(te.row0 + c) * g.B + q] = chs[6 * (at.ch0 + c)] * x;   // gamma |dOmega| chi^T t^0
+      Pg1[(size_t)(te.row0 + c) * g.B + q] = 0.0;
     }
   }
 }
@@ -269,10 +309,11 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, Real* A, R
                                           h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->d.status);
+                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.slab_n,
+                                                          h->wb.slab_map, h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
-                                          (Real*)h->wb.Pg[0], (Real*)h->wb.Pg[1]);
+                                          (double*)h->wb.Pg[0], (double*)h->wb.Pg[1]);
   SQ_LAUNCH_CHECK(h);
   k_wtable<Real><<<dim3(g.nslab, w.ntiles), 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.brick_list,
                                                           h->wb.brick_n, A, W);
@@ -288,7 +329,8 @@ int build_wave_entries(sq_handle* h, const Wave& w) {
   k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows, h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->d.status);
+                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.slab_n,
+                                                          h->wb.slab_map, h->d.status);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }

@@ -11,8 +11,9 @@
 //               the window mask and the recurrence update, and the nonlocal-stress partial
 //               sum_u W_b (grad_a t^j) (the gradient taps reuse the Laplacian loads). Then,
 //               fused, the projections gamma |dOmega| chi^T t^{j+1} of the new column: summed
-//               over the brick in registers, two warp shuffles, one shared-memory add per
-//               (image, channel, node), one global add per row and node per slab.
+//               over the brick in registers, a 3-shuffle reduce-scatter over the x-point lanes,
+//               one shared-memory add per (image, channel, node) issued by all 32 lanes at
+//               once, one global add per row and node per slab.
 //   k_moments   one block per tile: rho^j, K^j (restricted grad_a grad_b at the node),
 //               N^j = sum_rows chi(x_q) Pg^j, S^j = sum of the slab partials; FP64 table
 //               row; then clears Pg^j, which accumulates the projections of step j + 1.
@@ -131,6 +132,19 @@ k_apply_h(Geo g, Wave w, const Real* __restrict__ Tc, Real* __restrict__ Tn, con
 }
 
 // ------------------------------------------------------------------------------ sweep step
+// stencil weights of the sweep's precision, read straight from the kernel parameters
+template <typename Real> struct Coef;
+template <> struct Coef<float> {
+  static __device__ __forceinline__ float lap0(const Geo& g) { return g.lap0f; }
+  static __device__ __forceinline__ float lap(const Geo& g, int a, int p) { return g.lapf[a][p]; }
+  static __device__ __forceinline__ float grd(const Geo& g, int a, int p) { return g.grdf[a][p]; }
+};
+template <> struct Coef<double> {
+  static __device__ __forceinline__ double lap0(const Geo& g) { return g.lap0; }
+  static __device__ __forceinline__ double lap(const Geo& g, int a, int p) { return g.lap[a][p]; }
+  static __device__ __forceinline__ double grd(const Geo& g, int a, int p) { return g.grd[a][p]; }
+};
+
 template <typename Real> struct V4;
 template <> struct V4<float> { using T = float4; };
 template <> struct V4<double> { using T = double4_32a; };
@@ -155,48 +169,58 @@ constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x
 template <typename Real, int NO, bool kSmemP>
 __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
-       const Real* __restrict__ Pg, Real* __restrict__ Pg_next, const Real* __restrict__ Wt,
+       const double* __restrict__ Pg, double* __restrict__ Pg_next, const Real* __restrict__ Wt,
        const Real* __restrict__ chi, const Real* __restrict__ gdv, const int4* __restrict__ brec,
-       const int* __restrict__ n_rows, const int* __restrict__ bn, const Real* __restrict__ v,
-       const double* __restrict__ scal, int mode, double* __restrict__ Spart, int rows_smem) {
+       const int* __restrict__ slab_n, const int* __restrict__ slab_map, const int* __restrict__ bn,
+       const Real* __restrict__ v, const double* __restrict__ scal, int mode, double* __restrict__ Spart,
+       int rows_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[kThreads / 32][kTileB][9];
   __shared__ Real tn_sm[(kThreads / 32) * 16 * 32];
+  // wrapped V_eff index contributions of the slab's x, y and z positions (cell is periodic)
+  __shared__ int wrx[kMaxU], wry[kMaxU], wrz[kBrick];
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
-  Real* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
-  Real* Ps = kSmemP ? reinterpret_cast<Real*>(smem_raw) : Pn;               // [rows][8] projections
-  const Real* Pgs = kSmemP ? reinterpret_cast<Real*>(smem_raw) + (size_t)rows_smem * kTileB
-                           : Pg + (size_t)tl * g.r_cap * kTileB;           // [rows][8] Pg^j
+  double* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
+  // projections of t^{j+1}, summed in FP64 ([slab rows][8]); Pg^j staged in the sweep precision.
+  // In shared memory only the rows of the images that meet this slab are held (slab-local
+  // numbering, smap: slab row -> tile row); without it records index the tile rows directly.
+  double* Ps = kSmemP ? reinterpret_cast<double*>(smem_raw) : Pn;
+  const int nsr = kSmemP ? slab_n[(size_t)tl * g.nslab + slab] : 0;
+  const int* smap = slab_map + ((size_t)tl * g.nslab + slab) * g.r_cap;
+  Real* Pstage = reinterpret_cast<Real*>(reinterpret_cast<double*>(smem_raw) + (size_t)rows_smem * kTileB);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int o[3];
   tile_origin(g, t, o);
   const double f = (mode == 0) ? 0.5 : 1.0;
-  const Real ca = Real(f * scal[4]), cb = Real(f * scal[5]), cc = Real(mode == 0 ? 0.0 : 1.0);
+  // step coefficients: off-diagonal ca = 2/zeta, diagonal cd = ca lap0 + cb (cb = -2 chi/zeta)
+  const Real ca = Real(f * scal[4]), cd = Real(f * scal[6]), cc = Real(mode == 0 ? 0.0 : 1.0);
   const int Ux = g.U[0], Uy = g.U[1], Uz = g.U[2];
   const size_t tbase = (size_t)tl * g.Upts * kTileB;
   const Real* T = Tc + tbase;
-  const Real* Pt = Pg + (size_t)tl * g.r_cap * kTileB;
-  const int nrows = n_rows[tl];
+  const double* Pt = Pg + (size_t)tl * g.r_cap * kTileB;
   const bool project = (mode != 2);
   const int st[3] = {kTileB, Ux * kTileB, Ux * Uy * kTileB};
   const int Ua[3] = {Ux, Uy, Uz};
-  Real lap[3][NO + 1], grd[3][NO + 1];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int p = 1; p <= NO; ++p) {
-      lap[a][p] = Real(g.lap[a][p]);
-      grd[a][p] = Real(g.grd[a][p]);
-    }
-  const Real lap0 = Real(g.lap0);
+  for (int i = threadIdx.x; i < g.U[0] + g.U[1] + kBrick; i += kThreads) {
+    int a, u;
+    if (i < g.U[0]) { a = 0; u = i; }
+    else if (i < g.U[0] + g.U[1]) { a = 1; u = i - g.U[0]; }
+    else { a = 2; u = slab * kBrick + i - g.U[0] - g.U[1]; }
+    int wv = (o[a] - g.m[a] + u) % g.n[a];
+    if (wv < 0) wv += g.n[a];
+    if (a == 0) wrx[u] = wv;
+    else if (a == 1) wry[u] = wv * g.n[0];
+    else wrz[u - slab * kBrick] = wv * g.n[0] * g.n[1];
+  }
   if (kSmemP) {
-    Real* Pstage = const_cast<Real*>(Pgs);
-    for (int i = threadIdx.x; i < nrows * kTileB; i += kThreads) {
-      Pstage[i] = Pt[i];
-      if (project) Ps[i] = Real(0);
+    for (int i = threadIdx.x; i < nsr * kTileB; i += kThreads) {
+      Pstage[i] = Real(Pt[smap[i >> 3] * kTileB + (i & 7)]);
+      if (project) Ps[i] = 0.0;
     }
   }
   __syncthreads();
+  // without shared memory the apply reads Pg^j from global memory (FP64) directly
+  auto pg = [&](int idx) -> Real { return kSmemP ? Pstage[idx] : Real(Pt[idx]); };
 
   const int q = lane & 7, pa = lane >> 3;
   int qo[3];
@@ -219,30 +243,34 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     Real* tnv = tn_sm + warp * 16 * 32 + lane;   // per lane and brick point: V_nl t^j, then t^{j+1}
     // phase A: nonlocal apply, record-major: sum_rows chi_row(u) Pg^j[row][q] for the lane's
     // 16 points; the table loads of one record are independent of each other
-    {
-      Real ynl[16];
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {        // 8 points at a time keeps the accumulators in registers
+      Real ynl[8];
 #pragma unroll
-      for (int it = 0; it < 16; ++it) ynl[it] = Real(0);
+      for (int i = 0; i < 8; ++i) ynl[i] = Real(0);
       for (int k = 0; k < nb; ++k) {
         const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
-        const int nch = r0.w & 0xff, nchp = r0.w >> 8;
-        const unsigned long long mk64 = (unsigned long long)(unsigned)r1.z | ((unsigned long long)(unsigned)r1.w << 32);
+        const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
+        const int prow = kSmemP ? (int(unsigned(r0.w) >> 16)) : r0.y;
+        const unsigned mk = unsigned(half ? r1.w : r1.z) >> pa;   // bits pa + 4 i of this half
+        if (!(mk & 0x11111111u)) continue;
         for (int c0 = 0; c0 < nch; c0 += 4) {
           Real pv[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) pv[c] = (c0 + c < nch) ? Pgs[(r0.y + c0 + c) * kTileB + q] : Real(0);
+          for (int c = 0; c < 4; ++c) pv[c] = (c0 + c < nch) ? pg((prow + c0 + c) * kTileB + q) : Real(0);
 #pragma unroll
-          for (int it = 0; it < 16; ++it) {
-            if ((mk64 >> (pa + 4 * it)) & 1ull) {
+          for (int i = 0; i < 8; ++i) {
+            if ((mk >> (4 * i)) & 1u) {
+              const int it = 8 * half + i;
               Real cv[4];
               load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
-              ynl[it] += cv[0] * pv[0] + cv[1] * pv[1] + cv[2] * pv[2] + cv[3] * pv[3];
+              ynl[i] += cv[0] * pv[0] + cv[1] * pv[1] + cv[2] * pv[2] + cv[3] * pv[3];
             }
           }
         }
       }
 #pragma unroll
-      for (int it = 0; it < 16; ++it) tnv[it * 32] = ynl[it];
+      for (int i = 0; i < 8; ++i) tnv[(8 * half + i) * 32] = ynl[i];
     }
     __syncwarp();
 #pragma unroll 1
@@ -258,7 +286,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
         const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
         const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
         const Real tc = T[e];
-        Real y = lap0 * tc;
+        Real y = Real(0);                           // off-diagonal part of H t^j
         Real gr[3];
         const int u[3] = {ux, uy, uz};
 #pragma unroll
@@ -268,20 +296,14 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
           for (int pp = 1; pp <= NO; ++pp) {
             const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
             const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
-            y += lap[a][pp] * (fp + fm);
-            gr[a] += grd[a][pp] * (fp - fm);
+            y += Coef<Real>::lap(g, a, pp) * (fp + fm);
+            gr[a] += Coef<Real>::grd(g, a, pp) * (fp - fm);
           }
         }
-        {
-          const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
-          int wx = ax % g.n[0]; if (wx < 0) wx += g.n[0];
-          int wy = ay % g.n[1]; if (wy < 0) wy += g.n[1];
-          int wz = az % g.n[2]; if (wz < 0) wz += g.n[2];
-          y += v[(wz * g.n[1] + wy) * g.n[0] + wx] * tc;
-        }
+        const Real vloc = v[wrz[uz - slab * kBrick] + wry[uy] + wrx[ux]];   // V_eff at the wrapped node
         y += tnv[it * 32];                          // nonlocal part from phase A
         if (mode != 2) {
-          tn = ca * y + cb * tc - cc * tp;
+          tn = ca * y + (cd + ca * vloc) * tc - cc * tp;
           Tn[tbase + e] = tn;
         }
 #pragma unroll
@@ -296,36 +318,40 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
       tnv[it * 32] = tn;
     }
     __syncwarp();
-    // projections of t^{j+1} over this brick: each lane sums its 16 points in registers,
-    // two shuffles combine the 4 x-points, lanes 0..7 add one value per node
+    // projections of t^{j+1} over this brick: each lane sums its 16 points in registers, a
+    // reduce-scatter over the 4 x-point lanes (xor 8, then xor 16) leaves lane (pa, q) with the
+    // brick sum of channel c0 + pa for node q, so one FP64 conversion and one shared add per
+    // lane cover 4 channels x 8 nodes (FP64 instructions are narrow on this part)
     if (project) {
+      const bool b0 = (pa & 1) != 0, b1 = (pa & 2) != 0;
       for (int k = 0; k < nb; ++k) {
         const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
-        const int nch = r0.w & 0xff, nchp = r0.w >> 8;
+        const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
+        const int prow = kSmemP ? (int(unsigned(r0.w) >> 16)) : r0.y;
+        const unsigned mlo = unsigned(r1.z) >> pa, mhi = unsigned(r1.w) >> pa;
         for (int c0 = 0; c0 < nch; c0 += 4) {
           Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll 4
           for (int it = 0; it < 16; ++it) {
-            const int pbit = pa + 4 * it;
-            const unsigned mk = (pbit < 32) ? unsigned(r1.z) : unsigned(r1.w);
-            const Real tv = tnv[it * 32];
-            if (tv != Real(0) && ((mk >> (pbit & 31)) & 1u)) {
+            const unsigned bit = ((it < 8 ? mlo : mhi) >> (4 * (it & 7))) & 1u;
+            if (bit) {
+              const Real tv = tnv[it * 32];
               Real cv[4];
               load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
 #pragma unroll
               for (int c = 0; c < 4; ++c) acc[c] += cv[c] * tv;
             }
           }
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            if (c0 + c < nch) {
-              Real s = acc[c];
-              s += __shfl_xor_sync(0xffffffffu, s, 8);
-              s += __shfl_xor_sync(0xffffffffu, s, 16);
-              if (lane < 8 && s != Real(0))
-                atomicAdd(&Ps[(r0.y + c0 + c) * kTileB + lane], s * gdv[r0.z + c0 + c]);
-            }
-          }
+          // step 1 (pa bit 0): keep channels {b0, 2 + b0}, hand the other two to the partner
+          Real k0 = b0 ? acc[1] : acc[0], k1 = b0 ? acc[3] : acc[2];
+          const Real g0 = b0 ? acc[0] : acc[1], g1 = b0 ? acc[2] : acc[3];
+          k0 += __shfl_xor_sync(0xffffffffu, g0, 8);
+          k1 += __shfl_xor_sync(0xffffffffu, g1, 8);
+          // step 2 (pa bit 1): keep channel b0 + 2 b1 = pa
+          Real s = b1 ? k1 : k0;
+          s += __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 16);
+          const int c = c0 + pa;
+          if (c < nch && s != Real(0)) atomicAdd(&Ps[(prow + c) * kTileB + q], double(s * gdv[r0.z + c]));
         }
       }
     }
@@ -346,9 +372,9 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     Spart[(((size_t)tl * g.nslab + slab) * kTileB + qq) * 9 + k] = sv;
   }
   if (kSmemP && project) {
-    for (int idx = threadIdx.x; idx < nrows * kTileB; idx += kThreads) {
-      const Real s = Ps[idx];
-      if (s != Real(0)) atomicAdd(&Pn[idx], s);
+    for (int i = threadIdx.x; i < nsr * kTileB; i += kThreads) {
+      const double s = Ps[i];
+      if (s != 0.0) atomicAdd(&Pn[smap[i >> 3] * kTileB + (i & 7)], s);
     }
   }
 }
@@ -358,7 +384,7 @@ __constant__ int c_kpairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1
 // Moments of t^j per node (one warp per node), then Pg^j := 0 (the accumulator of step j + 1).
 template <typename Real>
 __global__ void __launch_bounds__(kThreads)
-k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restrict__ A, Real* __restrict__ Pg,
+k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restrict__ A, double* __restrict__ Pg,
           const int* __restrict__ n_rows, const double* __restrict__ Spart, double* __restrict__ mom) {
   const int tl = blockIdx.x, t = wave_tile(w, tl);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -367,7 +393,7 @@ k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restr
   const int B = g.B;
   const Real* T = Tj + (size_t)tl * g.Upts * B;
   const Real* At = A + (size_t)tl * g.r_cap * B;
-  Real* Pt = Pg + (size_t)tl * g.r_cap * B;
+  double* Pt = Pg + (size_t)tl * g.r_cap * B;
   const int nr = n_rows[tl];
   for (int q = warp; q < B; q += kThreads / 32) {
     int qo[3];
@@ -420,23 +446,28 @@ k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restr
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nr * B; i += kThreads) Pt[i] = Real(0);
+  for (int i = threadIdx.x; i < nr * B; i += kThreads) Pt[i] = 0.0;
 }
+
+constexpr int kStepSmemMax = 160 * 1024;   // dynamic shared memory of k_step with staged projections
 
 template <typename Real, int NO>
 static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
-                       const Real* Pg, Real* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
+                       const double* Pg, double* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                        int mode) {
-  const int rows_smem = int(smem / (2 * kTileB * sizeof(Real)));
-  if (smem <= 160 * 1024) {
-    // the kernel also holds static shared arrays: always opt in to the dynamic size
-    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const int rows_smem = int(smem / (kTileB * (sizeof(double) + sizeof(Real))));
+  if (smem <= kStepSmemMax) {
+    // the kernel also holds static shared arrays: always opt in. The attribute belongs to the
+    // function, not the launch, and handles on other host threads launch the same kernel, so
+    // every caller sets the same value (the largest dynamic size this path uses)
+    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kStepSmemMax));
     k_step<Real, NO, true><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
-                                                                h->wb.brick_rec, h->wb.n_rows, h->wb.brick_n, v,
+                                                                h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                                 h->d.scal, mode, h->wb.Spart, rows_smem);
   } else {
     k_step<Real, NO, false><<<grid, kThreads, 0, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
-                                                              h->wb.brick_rec, h->wb.n_rows, h->wb.brick_n, v,
+                                                              h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                               h->d.scal, mode, h->wb.Spart, 0);
   }
   SQ_LAUNCH_CHECK(h);
@@ -445,7 +476,7 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
 
 template <typename Real>
 static int dispatch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
-                         const Real* Pg, Real* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
+                         const double* Pg, double* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                          int mode) {
   switch (h->geo.n_o) {
     case 1: return launch_step<Real, 1>(h, w, grid, smem, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, v, mode);
@@ -462,19 +493,19 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
   Real* T[3] = {(Real*)h->wb.T[0], (Real*)h->wb.T[1], (Real*)h->wb.T[2]};
-  Real* Pg[2] = {(Real*)h->wb.Pg[0], (Real*)h->wb.Pg[1]};
+  double* Pg[2] = {(double*)h->wb.Pg[0], (double*)h->wb.Pg[1]};
   Real* A = (Real*)h->wb.A;
   Real* W = (Real*)h->wb.W;
   std::vector<int> nrows;
   for (const Wave& w : h->waves) {
     int rc = build_wave_lists(h, w);
     if (rc != SQ_OK) return rc;
-    // largest projector-row count of the wave sizes the per-slab shared accumulator
-    nrows.resize(w.ntiles);
-    SQ_CUDA_TRY(h, cudaMemcpyAsync(nrows.data(), h->wb.n_rows, sizeof(int) * w.ntiles, cudaMemcpyDeviceToHost, s));
+    // largest slab projector-row count of the wave sizes the per-slab shared accumulator
+    nrows.resize(size_t(w.ntiles) * g.nslab);
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(nrows.data(), h->wb.slab_n, sizeof(int) * nrows.size(), cudaMemcpyDeviceToHost, s));
     SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
     const int rmax = nrows.empty() ? 0 : *std::max_element(nrows.begin(), nrows.end());
-    const size_t smem = 2 * std::max<size_t>(1, size_t(rmax)) * kTileB * sizeof(Real);
+    const size_t smem = std::max<size_t>(1, size_t(rmax)) * kTileB * (sizeof(double) + sizeof(Real));
 
     const dim3 gstencil(g.nslab, w.ntiles);
     // algorithmic bytes of one stencil launch: node columns x region points x vectors moved

@@ -61,7 +61,7 @@ class sq_energies(C.Structure):
 
 class sq_result(C.Structure):
     _fields_ = [("tag", C.c_longlong), ("status", C.c_int), ("mu", C.c_double), ("energies", sq_energies),
-                ("sigma", C.c_double * 9), ("latency_ms", C.c_double)]
+                ("sigma", C.c_double * 9), ("latency_ms", C.c_double), ("error", C.c_char * 128)]
 
 
 class SQError(RuntimeError):
@@ -310,6 +310,7 @@ class Server:
         for i in range(n.value):
             r = buf[i]
             out.append({"tag": r.tag, "status": r.status, "mu": r.mu, "latency_ms": r.latency_ms,
+                        "error": r.error.decode(errors="replace"),
                         "sigma": np.array(list(r.sigma)).reshape(3, 3),
                         **{k: getattr(r.energies, k) for k, _ in sq_energies._fields_}})
         return out
