@@ -48,7 +48,31 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-requests", type=int, default=8,
                     help="requests in the served-stream measurement (0 disables it)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="only run two sweeps of the small profiling case (16^3 cell at the 40^3 "
+                         "workload's parameters and atom density) for a profiler capture; prints no bench line")
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """Two moment sweeps (device Lanczos bounds) of the small profiling case, nothing timed."""
+    import torch
+    from paper_2006_03697_gb300 import build
+    build.build()
+    from paper_2006_03697_gb300 import sq
+    from workloads import make_profile_case
+    prec = sq.SQ_MIXED if args.precision == "mixed" else sq.SQ_FP64
+    h = sq.sq_setup(sq.Desc(make_profile_case(), prec, bounds=None))
+    try:
+        for _ in range(2):
+            sq.sq_moments(h)
+        mu = sq.sq_fermi_level(h)
+        rho, en, sig = sq.sq_density_energy_stress(h, mu, 16 ** 3)
+    finally:
+        sq.sq_destroy(h)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "profile_4H_16cube", "mu": mu, "N_check": en["N_check"]}))
+    return 0
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -385,6 +409,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

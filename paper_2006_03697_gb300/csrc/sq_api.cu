@@ -404,6 +404,8 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   h->vol = desc->L[0] * desc->L[1] * desc->L[2];
   h->stream = (cudaStream_t)desc->stream;
   h->atoms_h = P.atoms;
+  h->proj4 = true;
+  for (const sq::AtomTab& at : P.atoms) h->proj4 = h->proj4 && at.nchp <= 4;
   h->table_len = P.table_len;
   h->n_ch_total = int(P.ch_l.size());
   h->wave_cap = P.wave_cap;

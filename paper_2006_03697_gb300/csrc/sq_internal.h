@@ -156,6 +156,7 @@ struct sq_handle {
   std::vector<sq::AtomTab> atoms_h;
   long long table_len = 0;
   int n_ch_total = 0;
+  bool proj4 = false;               // every atom has at most 4 projector channels (one group per image)
   std::vector<sq::Wave> waves;
   int wave_cap = 0;
   sq::Dev d;

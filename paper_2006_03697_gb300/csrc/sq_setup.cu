@@ -31,6 +31,7 @@ __global__ void k_chi_tables(Geo g, const AtomTab* __restrict__ atoms, const dou
       }
       chi[at.off + (long long)i * at.nchp + c] = Real(val);
     }
+    for (int c = at.nch; c < at.nchp; ++c) chi[at.off + (long long)i * at.nchp + c] = Real(0);   // padding
   }
 }
 

@@ -160,13 +160,42 @@ __device__ __forceinline__ void load4(const Real* p, Real out[4]) {
 
 constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x 8 nodes
 
+// ---- warp-level TF32 tensor-core products for the FP32 projector phases.
+// x = hi + lo with hi, lo TF32 (11 significant bits each); a product is taken as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation (the lo*lo term, ~2^-22 relative, is dropped).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+// d (16 x 8, FP32) += a (16 x 8, TF32, row) * b (8 x 8, TF32, col); fragment of lane (g, t),
+// g = lane / 4, t = lane % 4: a = {(g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4)},
+// b = {(t, g), (t + 4, g)}, d = {(g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1)}
+__device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_tf32x3(float d[4], const uint32_t ah[4], const uint32_t al[4],
+                                           const uint32_t bh[2], const uint32_t bl[2]) {
+  mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+
+// the brick's t values in the per-warp shared array: point p = a + 4 b + 16 c, node q
+__device__ __forceinline__ int tn_index(int p, int q) { return (p >> 2) * 32 + (p & 3) * kTileB + q; }
+
 // mode 0: t^1 = Hhat t^0;  mode 1: t^{j+1} = 2 Hhat t^j - t^{j-1};  mode 2: moments only.
 // Each warp walks whole 4^3 bricks of the slab: iteration it covers brick points
 // (a, b, c) = (lane >> 3, it & 3, it >> 2) for node q = lane & 7, so the 4 x-points of an
 // iteration are contiguous in memory and every image record is warp-uniform.
 // kSmemP: stage Pg^j and accumulate the slab's projections in shared memory (false when a
 // tile has too many projector rows; Pg^j is then read and Pg^{j+1} accumulated in global memory)
-template <typename Real, int NO, bool kSmemP>
+template <typename Real, int NO, bool kSmemP, bool kMMA>
 __global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
        const double* __restrict__ Pg, double* __restrict__ Pg_next, const Real* __restrict__ Wt,
@@ -241,36 +270,87 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
     const int nb = bn[(size_t)tl * g.nbricks + br];
     Real* tnv = tn_sm + warp * 16 * 32 + lane;   // per lane and brick point: V_nl t^j, then t^{j+1}
-    // phase A: nonlocal apply, record-major: sum_rows chi_row(u) Pg^j[row][q] for the lane's
-    // 16 points; the table loads of one record are independent of each other
+    if constexpr (kMMA) {
+      // phase A on tensor cores: Y[64 points][8 nodes] = X[64 points][4 nb rows] Pg^j[4 nb rows][8],
+      // X = the brick's projector values (zero outside each image's sphere). M = brick points
+      // (m-tile = one z-plane), N = the 8 nodes, K = 2 images x 4 channels per k-step, ordered so
+      // that each lane's A and B elements are two adjacent channels of one image:
+      // K = t -> (image k2 + t / 2, channel 2 (t % 2)), K = t + 4 -> the next channel.
+      const int g8 = lane >> 2, t4 = lane & 3, ch = 2 * (t4 & 1);
+      const int pa0 = g8 & 3, pb0 = g8 >> 2;         // lane's rows: points (pa0, pb0, c), (pa0, pb0 + 2, c)
+      float acc[4][4];
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[mt][i] = 0.f;
+      for (int k2 = 0; k2 < nb; k2 += 2) {
+        const int kr = k2 + (t4 >> 1);
+        int4 r0 = make_int4(0, 0, 0, 0), r1 = make_int4(0, 0, 0, 0);
+        if (kr < nb) {
+          r0 = rb[2 * kr];
+          r1 = rb[2 * kr + 1];
+        }
+        const int nch = r0.w & 0xff, prow = int(unsigned(r0.w) >> 16);
+        const float p0 = (ch < nch) ? float(Pstage[(prow + ch) * kTileB + g8]) : 0.f;
+        const float p1 = (ch + 1 < nch) ? float(Pstage[(prow + ch + 1) * kTileB + g8]) : 0.f;
+        uint32_t bh[2], bl[2];
+        split_tf32(p0, bh[0], bl[0]);
+        split_tf32(p1, bh[1], bl[1]);
+        const int dx = r1.x, plane = r1.x * r1.y * 4;
+        const float* xb = reinterpret_cast<const float*>(chi) + r0.x + (pb0 * dx + pa0) * 4 + ch;
+        const unsigned mlo = unsigned(r1.z) >> g8, mhi = unsigned(r1.w) >> g8;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+          const unsigned mw = (mt < 2) ? mlo : mhi;
+          const int sh = 16 * (mt & 1);
+          float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+          if ((mw >> sh) & 1u) x0 = *reinterpret_cast<const float2*>(xb + mt * plane);
+          if ((mw >> (sh + 8)) & 1u) x1 = *reinterpret_cast<const float2*>(xb + mt * plane + 8 * dx);
+          uint32_t ah[4], al[4];
+          split_tf32(x0.x, ah[0], al[0]);
+          split_tf32(x1.x, ah[1], al[1]);
+          split_tf32(x0.y, ah[2], al[2]);
+          split_tf32(x1.y, ah[3], al[3]);
+          mma_tf32x3(acc[mt], ah, al, bh, bl);
+        }
+      }
+      Real* tw = tn_sm + warp * 16 * 32;
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tw[tn_index(16 * mt + g8 + 8 * (i >> 1), 2 * t4 + (i & 1))] = Real(acc[mt][i]);
+    } else {
+      // phase A: nonlocal apply, record-major: sum_rows chi_row(u) Pg^j[row][q] for the lane's
+      // 16 points; the table loads of one record are independent of each other
 #pragma unroll 1
-    for (int half = 0; half < 2; ++half) {        // 8 points at a time keeps the accumulators in registers
-      Real ynl[8];
+      for (int half = 0; half < 2; ++half) {        // 8 points at a time keeps the accumulators in registers
+        Real ynl[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) ynl[i] = Real(0);
-      for (int k = 0; k < nb; ++k) {
-        const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
-        const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
-        const int prow = kSmemP ? (int(unsigned(r0.w) >> 16)) : r0.y;
-        const unsigned mk = unsigned(half ? r1.w : r1.z) >> pa;   // bits pa + 4 i of this half
-        if (!(mk & 0x11111111u)) continue;
-        for (int c0 = 0; c0 < nch; c0 += 4) {
-          Real pv[4];
+        for (int i = 0; i < 8; ++i) ynl[i] = Real(0);
+        for (int k = 0; k < nb; ++k) {
+          const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
+          const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
+          const int prow = kSmemP ? (int(unsigned(r0.w) >> 16)) : r0.y;
+          const unsigned mk = unsigned(half ? r1.w : r1.z) >> pa;   // bits pa + 4 i of this half
+          if (!(mk & 0x11111111u)) continue;
+          for (int c0 = 0; c0 < nch; c0 += 4) {
+            Real pv[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) pv[c] = (c0 + c < nch) ? pg((prow + c0 + c) * kTileB + q) : Real(0);
+            for (int c = 0; c < 4; ++c) pv[c] = (c0 + c < nch) ? pg((prow + c0 + c) * kTileB + q) : Real(0);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            if ((mk >> (4 * i)) & 1u) {
-              const int it = 8 * half + i;
-              Real cv[4];
-              load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
-              ynl[i] += cv[0] * pv[0] + cv[1] * pv[1] + cv[2] * pv[2] + cv[3] * pv[3];
+            for (int i = 0; i < 8; ++i) {
+              if ((mk >> (4 * i)) & 1u) {
+                const int it = 8 * half + i;
+                Real cv[4];
+                load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
+                ynl[i] += cv[0] * pv[0] + cv[1] * pv[1] + cv[2] * pv[2] + cv[3] * pv[3];
+              }
             }
           }
         }
-      }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) tnv[(8 * half + i) * 32] = ynl[i];
+        for (int i = 0; i < 8; ++i) tnv[(8 * half + i) * 32] = ynl[i];
+      }
     }
     __syncwarp();
 #pragma unroll 1
@@ -322,36 +402,84 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     // reduce-scatter over the 4 x-point lanes (xor 8, then xor 16) leaves lane (pa, q) with the
     // brick sum of channel c0 + pa for node q, so one FP64 conversion and one shared add per
     // lane cover 4 channels x 8 nodes (FP64 instructions are narrow on this part)
-    if (project) {
-      const bool b0 = (pa & 1) != 0, b1 = (pa & 2) != 0;
-      for (int k = 0; k < nb; ++k) {
-        const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
-        const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
-        const int prow = kSmemP ? (int(unsigned(r0.w) >> 16)) : r0.y;
-        const unsigned mlo = unsigned(r1.z) >> pa, mhi = unsigned(r1.w) >> pa;
-        for (int c0 = 0; c0 < nch; c0 += 4) {
-          Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
-#pragma unroll 4
-          for (int it = 0; it < 16; ++it) {
-            const unsigned bit = ((it < 8 ? mlo : mhi) >> (4 * (it & 7))) & 1u;
-            if (bit) {
-              const Real tv = tnv[it * 32];
-              Real cv[4];
-              load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
-#pragma unroll
-              for (int c = 0; c < 4; ++c) acc[c] += cv[c] * tv;
-            }
+    if constexpr (kMMA) {
+      if (project) {
+        // phase C on tensor cores: Pg^{j+1}[4 nb rows][8] += X^T[4 nb rows][64 points] t^{j+1}[64][8].
+        // M = 4 images x 4 channels per m-tile, ordered so each lane's A elements are two adjacent
+        // channels of one image (row g -> image m4 + g / 2, channel 2 (g % 2); row g + 8 -> the
+        // next channel), K = 8 brick points per k-step, N = the 8 nodes.
+        const int g8 = lane >> 2, t4 = lane & 3, ch = 2 * (g8 & 1);
+        const Real* tw = tn_sm + warp * 16 * 32;
+        for (int m4 = 0; m4 < nb; m4 += 4) {
+          const int kr = m4 + (g8 >> 1);
+          int4 r0 = make_int4(0, 0, 0, 0), r1 = make_int4(0, 0, 0, 0);
+          if (kr < nb) {
+            r0 = rb[2 * kr];
+            r1 = rb[2 * kr + 1];
           }
-          // step 1 (pa bit 0): keep channels {b0, 2 + b0}, hand the other two to the partner
-          Real k0 = b0 ? acc[1] : acc[0], k1 = b0 ? acc[3] : acc[2];
-          const Real g0 = b0 ? acc[0] : acc[1], g1 = b0 ? acc[2] : acc[3];
-          k0 += __shfl_xor_sync(0xffffffffu, g0, 8);
-          k1 += __shfl_xor_sync(0xffffffffu, g1, 8);
-          // step 2 (pa bit 1): keep channel b0 + 2 b1 = pa
-          Real s = b1 ? k1 : k0;
-          s += __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 16);
-          const int c = c0 + pa;
-          if (c < nch && s != Real(0)) atomicAdd(&Ps[(prow + c) * kTileB + q], double(s * gdv[r0.z + c]));
+          const int dx = r1.x, dy = r1.y;
+          const float* xb = reinterpret_cast<const float*>(chi) + r0.x + t4 * 4 + ch;   // point (t4, 0, 0)
+          const unsigned mlo = unsigned(r1.z) >> t4, mhi = unsigned(r1.w) >> t4;
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks) {
+            // points p0 = 8 ks + t4 = (t4, 2 (ks % 2), ks / 2) and p1 = p0 + 4 (one row further in b)
+            const unsigned mw = (ks < 4) ? mlo : mhi;
+            const int sh = 8 * (ks & 3);
+            const float* xp = xb + ((ks >> 1) * dy + 2 * (ks & 1)) * dx * 4;
+            float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
+            if ((mw >> sh) & 1u) x0 = *reinterpret_cast<const float2*>(xp);
+            if ((mw >> (sh + 4)) & 1u) x1 = *reinterpret_cast<const float2*>(xp + dx * 4);
+            uint32_t ah[4], al[4], bh[2], bl[2];
+            split_tf32(x0.x, ah[0], al[0]);
+            split_tf32(x0.y, ah[1], al[1]);
+            split_tf32(x1.x, ah[2], al[2]);
+            split_tf32(x1.y, ah[3], al[3]);
+            split_tf32(float(tw[tn_index(8 * ks + t4, g8)]), bh[0], bl[0]);
+            split_tf32(float(tw[tn_index(8 * ks + t4 + 4, g8)]), bh[1], bl[1]);
+            mma_tf32x3(d, ah, al, bh, bl);
+          }
+          const int nch = r0.w & 0xff, prow = int(unsigned(r0.w) >> 16);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int cc = ch + (i >> 1);
+            if (cc < nch && d[i] != 0.f)
+              atomicAdd(&Ps[(prow + cc) * kTileB + 2 * t4 + (i & 1)], double(d[i] * float(gdv[r0.z + cc])));
+          }
+        }
+      }
+    } else {
+      if (project) {
+        const bool b0 = (pa & 1) != 0, b1 = (pa & 2) != 0;
+        for (int k = 0; k < nb; ++k) {
+          const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
+          const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
+          const int prow = kSmemP ? (int(unsigned(r0.w) >> 16)) : r0.y;
+          const unsigned mlo = unsigned(r1.z) >> pa, mhi = unsigned(r1.w) >> pa;
+          for (int c0 = 0; c0 < nch; c0 += 4) {
+            Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll 4
+            for (int it = 0; it < 16; ++it) {
+              const unsigned bit = ((it < 8 ? mlo : mhi) >> (4 * (it & 7))) & 1u;
+              if (bit) {
+                const Real tv = tnv[it * 32];
+                Real cv[4];
+                load4(chi + r0.x + (((it >> 2) * r1.y + (it & 3)) * r1.x + pa) * nchp + c0, cv);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] += cv[c] * tv;
+              }
+            }
+            // step 1 (pa bit 0): keep channels {b0, 2 + b0}, hand the other two to the partner
+            Real k0 = b0 ? acc[1] : acc[0], k1 = b0 ? acc[3] : acc[2];
+            const Real g0 = b0 ? acc[0] : acc[1], g1 = b0 ? acc[2] : acc[3];
+            k0 += __shfl_xor_sync(0xffffffffu, g0, 8);
+            k1 += __shfl_xor_sync(0xffffffffu, g1, 8);
+            // step 2 (pa bit 1): keep channel b0 + 2 b1 = pa
+            Real s = b1 ? k1 : k0;
+            s += __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 16);
+            const int c = c0 + pa;
+            if (c < nch && s != Real(0)) atomicAdd(&Ps[(prow + c) * kTileB + q], double(s * gdv[r0.z + c]));
+          }
         }
       }
     }
@@ -460,13 +588,22 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
     // the kernel also holds static shared arrays: always opt in. The attribute belongs to the
     // function, not the launch, and handles on other host threads launch the same kernel, so
     // every caller sets the same value (the largest dynamic size this path uses)
-    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (sizeof(Real) == 4 && h->proj4) {
+      SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, sizeof(Real) == 4>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmemMax));
+      k_step<Real, NO, true, sizeof(Real) == 4><<<grid, kThreads, smem, h->stream>>>(
+          h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n,
+          v, h->d.scal, mode, h->wb.Spart, rows_smem);
+      SQ_LAUNCH_CHECK(h);
+      return SQ_OK;
+    }
+    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
-    k_step<Real, NO, true><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+    k_step<Real, NO, true, false><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
                                                                 h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                                 h->d.scal, mode, h->wb.Spart, rows_smem);
   } else {
-    k_step<Real, NO, false><<<grid, kThreads, 0, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+    k_step<Real, NO, false, false><<<grid, kThreads, 0, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
                                                               h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                               h->d.scal, mode, h->wb.Spart, 0);
   }

@@ -8,6 +8,7 @@ from .sq_workloads import (  # noqa: F401
     CONFIGS,
     make_instance,
     make_batch,
+    make_profile_case,
     tiny_instance,
     gaussian_veff,
     random_positions,

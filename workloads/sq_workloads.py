@@ -146,6 +146,16 @@ def make_instance(config: int, instance: int = 0) -> dict:
     raise ValueError(f"no single-instance config {config}")
 
 
+def make_profile_case(instance: int = 0) -> dict:
+    """The 40^3 / 64 H workload's parameters (h = 0.3, n_o = 6, s+p, R_cut = 4, kT, atom
+    density 0.037 / bohr^3) on a 16^3-node cell with 4 atoms and n_pl = 4: the same per-tile
+    work in a case small enough (about 2.5 GB on the device) for a profiler capture."""
+    rng = _rng(9, instance)
+    pos = random_positions(rng, 4, [4.8] * 3)
+    return _instance("profile_4H_16cube", [4.8] * 3, [16] * 3, 6, pos,
+                     [s_proj(0.5, 1.0), p_proj(0.5, 0.5)], KT_1E6_K, 4, 4.0, 4)
+
+
 def make_batch(config: int = 4, count: int = 32, h: float = 0.3, start: int = 0,
                atom_choices=(32, 64, 128, 256, 512), p_large: float | None = None) -> list:
     """Uneven quantum-MD-like snapshots: atom count from atom_choices (or 512 with
