@@ -442,6 +442,16 @@ def contract(prob: Problem, mom: np.ndarray, mu: float, lam_lo: float, lam_hi: f
             S_ab = float(np.sum(mom[:, :, 8 + 3 * a + b] @ cw))
             sig_III[a, b] = -2.0 * ((E_nl / 2.0 if a == b else 0.0) + 2.0 * S_ab)
     sigma = (sig_I + sig_III) / prob.vol
+    # App. A (Eq. ON:Pressure and its SQ form), restricted to the kinetic and nonlocal terms:
+    # the first term -4 sum_q sum' (chi c^j + zeta d^j) rho^j_q is -4 tr(D H) = -2 E_band; its
+    # V_eff part -2 |dOmega| sum_q V_q rho_q belongs with the exchange-correlation and
+    # electrostatic terms (outside this path) and is taken out, leaving -4 tr(D (H - V_eff));
+    # the nonlocal term -2 sum_q w_q^T V_nl,q (sum' c^j t^j + 2 (X - R) . grad sum' c^j t^j)
+    # is -E_nl - 4 sum_q sum' c^j (S^j_xx + S^j_yy + S^j_zz).
+    E_pot = prob.dV * float(np.sum(prob.v.reshape(-1) * rho))
+    trS = float(np.sum((mom[:, :, 8] + mom[:, :, 12] + mom[:, :, 16]) @ cw))
+    bracket = -2.0 * (E_band - E_pot) - E_nl - 4.0 * trS
+    pressure_A = -bracket / (3.0 * prob.vol)
     return {
         "rho": rho,
         "E_band": E_band,
@@ -453,6 +463,8 @@ def contract(prob: Problem, mom: np.ndarray, mu: float, lam_lo: float, lam_hi: f
         "sigma_I": sig_I / prob.vol,
         "sigma_III": sig_III / prob.vol,
         "pressure": -float(np.trace(sigma)) / 3.0,
+        "E_pot": E_pot,
+        "pressure_A": pressure_A,
     }
 
 

@@ -334,3 +334,66 @@ def test_config1_instance_shape():
     prob = Problem(inst)
     assert list(prob.m) == [6, 6, 6] and prob.Nc == 13 ** 3 and prob.Nd == 1728
     assert Problem(make_instance(2)).Nc == 27 ** 3
+
+
+# ---------------------------------------------------------------- P10: App. A pressure
+def test_p10_pressure_free_electrons_is_grand_potential_volume_derivative():
+    """V = 0, no projectors: the App. A pressure (kinetic part 2 E_kin / (3 |Omega|)) equals
+    -d(Omega_grand)/d|Omega| at fixed mu under isotropic scaling of the grid, from the
+    Brillouin-zone closed forms: P = -(omega + (h/3) d omega/dh), omega = e + e_s - mu rho."""
+    h = 1.0
+    inst = tiny_instance(seed=5, n=(3, 3, 3), h=(h, h, h), n_atoms=0, n_o=2, kT=3.17, r_cut=6.0,
+                         n_pl=40, proj=[], vdepth=0.0, n_e=10.0)
+    inst["proj"] = [[]]
+    prob = Problem(inst)
+    lo, hi = -0.05, 8.2
+    mom = node_moments(prob, np.array([0, 0, 0]), lo, hi)
+    mom_all = np.repeat(mom[None], prob.Nd, axis=0)
+    mu = fermi_bisect(mom_all[:, :, 0].sum(0), prob.n_e, prob.kT, lo, hi, prob.M)
+    out = contract(prob, mom_all, mu, lo, hi)
+
+    def omega(hh):
+        b = free_electron.bz_values(mu, prob.kT, (hh, hh, hh), prob.n_o)
+        return b["E_band_density"] + b["E_s_density"] - mu * b["rho"]
+
+    def dcentral(dh):
+        return (omega(h + dh) - omega(h - dh)) / (2.0 * dh)
+
+    dh = 1e-3 * h
+    domega = (4.0 * dcentral(dh / 2) - dcentral(dh)) / 3.0      # Richardson: O(dh^4)
+    p_bz = -(omega(h) + h / 3.0 * domega)
+    assert abs(out["pressure_A"] - p_bz) < 1e-9 * abs(p_bz)
+    # a dropped 2/3 (or a sign) in the kinetic part would miss by O(1)
+    assert abs(out["pressure_A"] - out["E_band"] / prob.vol) > 0.1 * abs(p_bz)
+    assert abs(out["E_pot"]) == 0.0
+
+
+def test_p10_pressure_equals_trace_stress_with_second_difference_kinetic_term():
+    """With nonlocal projectors and a potential: the App. A pressure equals -tr(sigma)/3 when
+    the kinetic moments grad_a grad_a are replaced by the second-difference stencil D2_a (the
+    operator in H), up to the Chebyshev truncation of the band-energy form (reading: the
+    V_eff part of tr(DH) is left to the terms outside this path). The truncation part
+    vanishes as n_pl grows; the paper-form trace differs by the restricted-gradient kinetic
+    moments (m < 2 n_o here)."""
+    diffs = []
+    for n_pl in (12, 24):
+        inst = tiny_instance(seed=11, n=(4, 4, 4), h=(0.8, 0.8, 0.8), n_atoms=3, n_o=3, r_cut=2.4, n_pl=n_pl)
+        prob = Problem(inst)
+        lo, hi = lanczos_bounds(prob)
+        moms, l2s = [], []
+        for q in range(prob.Nd):
+            m, l2 = node_moments(prob, np.array([q % 4, (q // 4) % 4, q // 16]), lo, hi, with_d2=True)
+            moms.append(m)
+            l2s.append(l2)
+        mom, l2 = np.array(moms), np.array(l2s)
+        mu = fermi_bisect(mom[:, :, 0].sum(0), prob.n_e, prob.kT, lo, hi, prob.M)
+        out = contract(prob, mom, mu, lo, hi)
+        c, _, _ = fd_coefficients(mu, prob.kT, 0.5 * (hi + lo), 0.5 * (hi - lo), prob.n_pl, prob.M)
+        cw = primed(prob.n_pl) * c
+        sig_d2 = out["sigma"].copy() * prob.vol
+        for a in range(3):
+            sig_d2[a, a] += 2.0 * float(np.sum(l2[:, :, a] @ cw)) - 2.0 * float(np.sum(mom[:, :, 1 + a] @ cw))
+        p_trace = -float(np.trace(sig_d2)) / (3.0 * prob.vol)
+        diffs.append(abs(out["pressure_A"] - p_trace))
+    assert diffs[1] < 1e-12 * abs(out["pressure_A"])
+    assert diffs[0] > diffs[1]
