@@ -372,11 +372,13 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == sq.SQ_MIXED else "f64", "data": "synthetic",
         "config": {"workload": CONFIG_NAME, "precision": args.precision, "bounds": "lanczos (device, per step)",
-                   "node_columns_per_step": nd, "flush_l2": "no flush: per-wave working set (~9 GB) > L2"},
+                   "node_columns_per_step": nd,
+                   "flush_l2": f"no flush: device working set {sq.sq_footprint_bytes(desc) / 1e9:.1f} GB > L2"},
         "node_columns_per_s": value * nd,
         "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
         "kernels": kern, "energies": {k: en[k] for k in ("E_band", "E_s", "E_nl", "F", "N_check", "mu")},
         "sigma": sig_dev.cpu().numpy().reshape(3, 3).tolist(),
+        "pressure_app_a": sq.sq_pressure(h, en["mu"])[0],
     }
     if args.fp64_compare and rank == 0:
         d64 = sq.Desc(inst, sq.SQ_FP64, bounds=None, stream=sptr)

@@ -142,6 +142,19 @@ int sq_density_energy_stress(sq_handle* h, double mu, double* rho_out, sq_energi
 int sq_density_energy_stress_dev(sq_handle* h, double mu, double* rho_dev, sq_energies* e_out,
                                  double* sigma_dev);
 
+/* Pressure only (App. A, Eq. ON:Pressure and its SQ form) restricted to the kinetic and
+ * nonlocal terms: the band term -4 sum_q sum'_j (chi c^j + zeta d^j) rho^j_q = -2 E_band less its
+ * V_eff part, and the nonlocal term -2 sum_q w_q^T V_nl,q (sum' c^j t^j + 2 (X - R).grad sum' c^j t^j):
+ *   P = (2 (E_band - E_pot) + E_nl + 4 sum_q sum'_j c^j (S^j_xx + S^j_yy + S^j_zz)_q) / (3 |Omega|)
+ * in Ha/bohr^3, with E_pot = |dOmega| sum_q V_eff(x_q) rho_q (Ha), the V_eff part of the band
+ * energy, which the paper's formula pairs with the exchange-correlation and electrostatic
+ * terms outside this library. Needs no second derivatives of the density matrix (the K^j
+ * moments are not used); equals -tr(sigma)/3 when sigma's kinetic moments are taken with
+ * the second-difference operator of H, up to the Chebyshev truncation of E_band.
+ * Host outputs: pressure_out (required), e_pot_out or NULL. Synchronises the stream.
+ * Errors: SQ_ERR_STATE (no moments), SQ_ERR_INVALID_ARG (NULL pressure_out, non-finite mu). */
+int sq_pressure(sq_handle* h, double mu, double* pressure_out, double* e_pot_out);
+
 /* Bounds in use (after sq_moments in Lanczos mode). */
 int sq_get_bounds(const sq_handle* h, double* lambda_lo, double* lambda_hi);
 

@@ -163,7 +163,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   int ch = 0;
   long long e_cap = 0, r_cap = 0, br_cap = 0;
   for (int J = 0; J < d->n_atoms; ++J) {
-    sq::AtomTab at;
+    sq::AtomTab at{};
     std::memset(&at, 0, sizeof(at));
     int s = d->species[J];
     double rc_max = 0.0;
@@ -192,6 +192,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
       at.lo[a] = int(std::ceil((R - rc_max) / g.h[a]));
       int hi = int(std::floor((R + rc_max) / g.h[a]));
       at.dim[a] = std::max(0, hi - at.lo[a] + 1);
+      at.dlo[a] = float(at.lo[a] * g.h[a] - R);
       boxpts *= at.dim[a];
     }
     if (at.nch == 0) boxpts = 0;
@@ -265,10 +266,13 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
                                        nst * g.B * size_t(5 * k + 8)) + sizeof(int) * nst;
     P.fixed_bytes += sizeof(double) * size_t(P.table_len);   // FP64 tables for the Lanczos apply
   }
-  // tiles per wave: keep the per-wave working set near 8 GiB
-  size_t budget = size_t(8) << 30;
+  // tiles per wave: keep the per-wave working set under 24 GiB (fewer, larger launches: less
+  // per-wave setup and a smaller tail), with the tiles spread evenly over the waves
+  size_t budget = size_t(24) << 30;
   long long wc = std::max<long long>(1, (long long)(budget / std::max<size_t>(P.per_tile_bytes, 1)));
-  P.wave_cap = int(std::min<long long>(std::min<long long>(wc, g.n_tiles), 32768));
+  wc = std::min<long long>(std::min<long long>(wc, g.n_tiles), 32768);
+  const long long nwaves = (g.n_tiles + wc - 1) / wc;
+  P.wave_cap = int((g.n_tiles + nwaves - 1) / nwaves);
   P.wave_cap = std::max<int>(P.wave_cap, int(P.lz_tiles.size()));
   return SQ_OK;
 }
@@ -555,13 +559,17 @@ int sq_fermi_level(sq_handle* h, double* mu_out) {
 }
 
 static int contraction_common(sq_handle* h, double mu, double* rho_dev, sq_energies* e_out,
-                              double* sigma_host, double* sigma_dev) {
+                              double* sigma_host, double* sigma_dev, double* pressure_host = nullptr) {
   if (!h) return SQ_ERR_INVALID_ARG;
   if (!h->moments_ready) return sq::fail(h, SQ_ERR_STATE, "contraction before sq_moments");
   if (!std::isfinite(mu)) return sq::fail(h, SQ_ERR_INVALID_ARG, "mu is not finite");
   double out[16];
-  int rc = sq::run_contraction(h, mu, rho_dev, (e_out || sigma_host) ? out : nullptr);
+  int rc = sq::run_contraction(h, mu, rho_dev, (e_out || sigma_host || pressure_host) ? out : nullptr);
   if (rc != SQ_OK) return rc;
+  if (pressure_host) {
+    pressure_host[0] = out[14];
+    pressure_host[1] = out[13];
+  }
   if (e_out) {
     e_out->E_band = out[0];
     e_out->E_s = out[1];
@@ -591,6 +599,16 @@ int sq_density_energy_stress(sq_handle* h, double mu, double* rho_out, sq_energi
 int sq_density_energy_stress_dev(sq_handle* h, double mu, double* rho_dev, sq_energies* e_out, double* sigma_dev) {
   if (!h) return SQ_ERR_INVALID_ARG;
   return contraction_common(h, mu, rho_dev ? rho_dev : h->d.rho, e_out, nullptr, sigma_dev);
+}
+
+int sq_pressure(sq_handle* h, double mu, double* pressure_out, double* e_pot_out) {
+  if (!h || !pressure_out) return SQ_ERR_INVALID_ARG;
+  double pe[2];
+  int rc = contraction_common(h, mu, h->d.rho, nullptr, nullptr, nullptr, pe);
+  if (rc != SQ_OK) return rc;
+  *pressure_out = pe[0];
+  if (e_pot_out) *e_pot_out = pe[1];
+  return SQ_OK;
 }
 
 int sq_get_bounds(const sq_handle* h, double* lo, double* hi) {

@@ -42,6 +42,8 @@ struct AtomTab {
   int pad;
   long long off;    // table offset; channel c of box point li at off + li * nchp + c
   double R[3];      // base image position (wrapped into the cell)
+  float dlo[3];     // lo_a h_a - R_a: x_a - R_a of box point l is l_a h_a + dlo[a] (any image)
+  int pad2;
 };
 
 struct TileEntry {

@@ -109,11 +109,11 @@ __global__ void k_coef(const double* __restrict__ scal, double kT, int n_pl, int
   }
 }
 
-constexpr int kNPart = 19;
+constexpr int kNPart = 20;
 
 __global__ void k_contract(const double* __restrict__ mom, const double* __restrict__ coef,
-                           const double* __restrict__ scal, int Nd, int n_pl, double dV, double* __restrict__ rho,
-                           double* __restrict__ part) {
+                           const double* __restrict__ scal, const double* __restrict__ v, int Nd, int n_pl,
+                           double dV, double* __restrict__ rho, double* __restrict__ part) {
   __shared__ double sh[256];
   const double lam_lo = scal[0], lam_hi = scal[1];
   const double chi_q = 0.5 * (lam_hi + lam_lo), zeta_q = 0.5 * (lam_hi - lam_lo);
@@ -139,6 +139,7 @@ __global__ void k_contract(const double* __restrict__ mom, const double* __restr
     }
     rho[q] = 2.0 / dV * r;
     loc[18] = r;
+    loc[19] = v[q] * r;   // |dOmega| V_q rho_q / 2
     for (int k = 0; k < kNPart; ++k) acc[k] += loc[k];
   }
   for (int k = 0; k < kNPart; ++k) {
@@ -147,7 +148,10 @@ __global__ void k_contract(const double* __restrict__ mom, const double* __restr
   }
 }
 
-// out (scal + 16): [E_band, E_s, E_nl, N_check, sigma(9, row-major)]
+// out (scal + 16): [E_band, E_s, E_nl, N_check, sigma(9, row-major), E_pot, P]
+// E_pot = |dOmega| sum_q V_q rho_q; P = the App. A pressure restricted to the kinetic and
+// nonlocal terms: -(1/(3|Omega|)) [-2 (E_band - E_pot) - E_nl - 4 sum_q sum' c^j tr S^j_q]
+// (the V_eff part of -4 tr(D H) goes with the exchange-correlation / electrostatic terms)
 __global__ void k_contract_final(const double* __restrict__ part, int nblk, double kT, double vol,
                                  double* __restrict__ scal) {
   if (threadIdx.x != 0) return;
@@ -172,6 +176,9 @@ __global__ void k_contract_final(const double* __restrict__ part, int nblk, doub
     for (int b = 0; b < 3; ++b)
       sig[3 * a + b] += -2.0 * ((a == b ? 0.5 * E_nl : 0.0) + 2.0 * tot[9 + 3 * a + b]);
   for (int k = 0; k < 9; ++k) out[4 + k] = sig[k] / vol;
+  const double E_pot = 2.0 * tot[19];
+  out[13] = E_pot;
+  out[14] = -(-2.0 * (out[0] - E_pot) - E_nl - 4.0 * (tot[9] + tot[13] + tot[17])) / (3.0 * vol);
 }
 
 __global__ void k_set_scalar(double* __restrict__ scal, int idx, double v) { scal[idx] = v; }
@@ -203,12 +210,12 @@ int run_contraction(sq_handle* h, double mu, double* rho_dev, double* out_host) 
   k_coef<<<3, 256, sizeof(double) * h->M, s>>>(h->d.scal, h->kT, g.n_pl, h->M, h->d.coef);
   SQ_LAUNCH_CHECK(h);
   const int nblk = std::min(1024, (h->Nd + 255) / 256);
-  k_contract<<<nblk, 256, 0, s>>>(h->d.mom, h->d.coef, h->d.scal, h->Nd, g.n_pl, g.dV, rho_dev, h->d.part);
+  k_contract<<<nblk, 256, 0, s>>>(h->d.mom, h->d.coef, h->d.scal, h->d.v64, h->Nd, g.n_pl, g.dV, rho_dev, h->d.part);
   SQ_LAUNCH_CHECK(h);
   k_contract_final<<<1, 32, 0, s>>>(h->d.part, nblk, h->kT, h->vol, h->d.scal);
   SQ_LAUNCH_CHECK(h);
   if (out_host) {
-    SQ_CUDA_TRY(h, cudaMemcpyAsync(out_host, h->d.scal + 16, 13 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(out_host, h->d.scal + 16, 15 * sizeof(double), cudaMemcpyDeviceToHost, s));
     SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
   }
   return SQ_OK;

@@ -243,7 +243,7 @@ __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
 // W_b(u, q) = sum_rows gamma |dOmega| A[row][q] chi_row(u) (x_u,b - R_b) on the window of q:
 // contracting the atom sum of the sigma^III term once, S^j_ab = sum_u W_b(u,q) (grad_a t^j)(u).
 template <typename Real>
-__global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ chs,
+__global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const Real* __restrict__ gdv,
                          const Real* __restrict__ chi,
                          const TileEntry* __restrict__ entries, const int* __restrict__ blist,
                          const int* __restrict__ bn, const Real* __restrict__ A, Real* __restrict__ W) {
@@ -255,6 +255,7 @@ __global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
   const TileEntry* ent = entries + (size_t)tl * g.e_cap;
   const Real* At = A + (size_t)tl * g.r_cap * g.B;
   Real* Wt = W + (size_t)tl * 3 * g.Upts * g.B;
+  const Real hr[3] = {Real(g.h[0]), Real(g.h[1]), Real(g.h[2])};
   for (int i = threadIdx.x; i < nel; i += blockDim.x) {
     const int q = i % g.B, p = i / g.B;
     const int ux = p % g.U[0], uy = (p / g.U[0]) % g.U[1], uz = z0 + p / (g.U[0] * g.U[1]);
@@ -263,22 +264,30 @@ __global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
     node_offset(g, q, qo);
     Real acc[3] = {Real(0), Real(0), Real(0)};
     if (node_valid(g, o, qo) && in_window(g, qo, ux, uy, uz)) {
-      const int ax = o[0] - g.m[0] + ux, ay = o[1] - g.m[1] + uy, az = o[2] - g.m[2] + uz;
+      const int ax[3] = {o[0] - g.m[0] + ux, o[1] - g.m[1] + uy, o[2] - g.m[2] + uz};
       const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
       const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
       const int nb = bn[(size_t)tl * g.nbricks + br];
-      const double x[3] = {ax * g.h[0], ay * g.h[1], az * g.h[2]};
       for (int k = 0; k < nb; ++k) {
         const TileEntry te = ent[lst[k]];
-        const AtomTab at = atoms[te.atom];
-        const int li = box_index(at, te.s, g.n, ax, ay, az);
-        if (li < 0) continue;
-        const Real* cr = chi_row(chi, at, li);
+        const AtomTab& at = atoms[te.atom];
+        int l[3];
+        bool in = true;
+        for (int b = 0; b < 3; ++b) {
+          l[b] = ax[b] - te.s[b] * g.n[b] - at.lo[b];
+          in = in && (unsigned)l[b] < (unsigned)at.dim[b];
+        }
+        if (!in) continue;
+        const Real* cr = chi_row(chi, at, (l[2] * at.dim[1] + l[1]) * at.dim[0] + l[0]);
         Real cs = Real(0);   // accumulated in the sweep's precision (FP32 suffices for the mixed path)
-        for (int c = 0; c < at.nch; ++c)
-          cs += Real(chs[6 * (at.ch0 + c)]) * At[(size_t)(te.row0 + c) * g.B + q] * cr[c];
+        for (int c = 0; c < at.nch; ++c) cs += gdv[at.ch0 + c] * At[(size_t)(te.row0 + c) * g.B + q] * cr[c];
         if (cs == Real(0)) continue;
-        for (int b = 0; b < 3; ++b) acc[b] += cs * Real(x[b] - (at.R[b] + te.s[b] * g.L[b]));
+        // x_b - R_b of the image: l_b h_b + (lo_b h_b - R_b) (the image shift s n h = s L cancels)
+        for (int b = 0; b < 3; ++b) {
+          const Real d = (sizeof(Real) == 4) ? Real(l[b]) * hr[b] + Real(at.dlo[b])
+                                             : Real((at.lo[b] + l[b]) * g.h[b] - at.R[b]);
+          acc[b] += cs * d;
+        }
       }
     }
     for (int b = 0; b < 3; ++b) Wt[((size_t)b * g.Upts + pt) * g.B + q] = acc[b];
@@ -303,7 +312,7 @@ __global__ void k_init_t0(Geo g, Wave w, Real* __restrict__ T0) {
 }
 
 template <typename Real>
-static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, Real* A, Real* W, Real* T0) {
+static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, const Real* gdvR, Real* A, Real* W, Real* T0) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
   k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows,
@@ -316,7 +325,7 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, Real* A, R
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
                                           (double*)h->wb.Pg[0], (double*)h->wb.Pg[1]);
   SQ_LAUNCH_CHECK(h);
-  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.brick_list,
+  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 256, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries, h->wb.brick_list,
                                                           h->wb.brick_n, A, W);
   SQ_LAUNCH_CHECK(h);
   k_init_t0<Real><<<1024, 256, 0, s>>>(g, w, T0);
@@ -349,8 +358,8 @@ int build_tables(sq_handle* h) {
 
 int build_wave_lists(sq_handle* h, const Wave& w) {
   if (h->precision == SQ_FP64)
-    return wave_lists_t<double>(h, w, h->d.chi64, (double*)h->wb.A, (double*)h->wb.W, (double*)h->wb.T[0]);
-  return wave_lists_t<float>(h, w, h->d.chi32, (float*)h->wb.A, (float*)h->wb.W, (float*)h->wb.T[0]);
+    return wave_lists_t<double>(h, w, h->d.chi64, h->d.gdv64, (double*)h->wb.A, (double*)h->wb.W, (double*)h->wb.T[0]);
+  return wave_lists_t<float>(h, w, h->d.chi32, h->d.gdv32, (float*)h->wb.A, (float*)h->wb.W, (float*)h->wb.T[0]);
 }
 
 }  // namespace sq

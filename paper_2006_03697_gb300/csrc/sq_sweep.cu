@@ -179,13 +179,6 @@ __device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], const 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ void mma_tf32x3(float d[4], const uint32_t ah[4], const uint32_t al[4],
-                                           const uint32_t bh[2], const uint32_t bl[2]) {
-  mma_tf32(d, al, bh);
-  mma_tf32(d, ah, bl);
-  mma_tf32(d, ah, bh);
-}
-
 // the brick's t values in the per-warp shared array: point p = a + 4 b + 16 c, node q
 __device__ __forceinline__ int tn_index(int p, int q) { return (p >> 2) * 32 + (p & 3) * kTileB + q; }
 
@@ -195,17 +188,33 @@ __device__ __forceinline__ int tn_index(int p, int q) { return (p >> 2) * 32 + (
 // iteration are contiguous in memory and every image record is warp-uniform.
 // kSmemP: stage Pg^j and accumulate the slab's projections in shared memory (false when a
 // tile has too many projector rows; Pg^j is then read and Pg^{j+1} accumulated in global memory)
+constexpr int kStepThreads = 256;   // most threads of a k_step block (its warps walk the slab's bricks)
+
+// Warps per k_step block: 4..8, the count that leaves the fewest idle warp-turns over the
+// slab's bricks (49 bricks -> 7 warps, 16 -> 8, 36 -> 6); ties go to more warps.
+static int step_warps(int bricks_per_slab) {
+  int best = kStepThreads / 32, idle_best = 1 << 30;
+  for (int w = kStepThreads / 32; w >= 4; --w) {
+    const int idle = (bricks_per_slab + w - 1) / w * w - bricks_per_slab;
+    if (idle < idle_best) {
+      idle_best = idle;
+      best = w;
+    }
+  }
+  return best;
+}
+
 template <typename Real, int NO, bool kSmemP, bool kMMA>
-__global__ void __launch_bounds__(kThreads, sizeof(Real) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kStepThreads, sizeof(Real) == 4 ? 3 : 2)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
        const double* __restrict__ Pg, double* __restrict__ Pg_next, const Real* __restrict__ Wt,
        const Real* __restrict__ chi, const Real* __restrict__ gdv, const int4* __restrict__ brec,
        const int* __restrict__ slab_n, const int* __restrict__ slab_map, const int* __restrict__ bn,
        const Real* __restrict__ v, const double* __restrict__ scal, int mode, double* __restrict__ Spart,
        int rows_smem) {
+  // dynamic shared memory: [Ps: rows_smem x 8 FP64][red: nw x 8 x 9 FP64][Pstage: rows_smem x 8]
+  // [tn_sm: nw x 16 x 32] (Ps and Pstage only with kSmemP; rows_smem = 0 otherwise)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[kThreads / 32][kTileB][9];
-  __shared__ Real tn_sm[(kThreads / 32) * 16 * 32];
   // wrapped V_eff index contributions of the slab's x, y and z positions (cell is periodic)
   __shared__ int wrx[kMaxU], wry[kMaxU], wrz[kBrick];
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
@@ -216,8 +225,10 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   double* Ps = kSmemP ? reinterpret_cast<double*>(smem_raw) : Pn;
   const int nsr = kSmemP ? slab_n[(size_t)tl * g.nslab + slab] : 0;
   const int* smap = slab_map + ((size_t)tl * g.nslab + slab) * g.r_cap;
-  Real* Pstage = reinterpret_cast<Real*>(reinterpret_cast<double*>(smem_raw) + (size_t)rows_smem * kTileB);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* red = reinterpret_cast<double*>(smem_raw) + (size_t)rows_smem * kTileB;        // S partials [nw][8][9]
+  Real* Pstage = reinterpret_cast<Real*>(red + nw * kTileB * 9);
+  Real* tn_sm = Pstage + (size_t)rows_smem * kTileB;                                      // [nw][16][32]
   int o[3];
   tile_origin(g, t, o);
   const double f = (mode == 0) ? 0.5 : 1.0;
@@ -230,7 +241,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   const bool project = (mode != 2);
   const int st[3] = {kTileB, Ux * kTileB, Ux * Uy * kTileB};
   const int Ua[3] = {Ux, Uy, Uz};
-  for (int i = threadIdx.x; i < g.U[0] + g.U[1] + kBrick; i += kThreads) {
+  for (int i = threadIdx.x; i < g.U[0] + g.U[1] + kBrick; i += blockDim.x) {
     int a, u;
     if (i < g.U[0]) { a = 0; u = i; }
     else if (i < g.U[0] + g.U[1]) { a = 1; u = i - g.U[0]; }
@@ -242,7 +253,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     else wrz[u - slab * kBrick] = wv * g.n[0] * g.n[1];
   }
   if (kSmemP) {
-    for (int i = threadIdx.x; i < nsr * kTileB; i += kThreads) {
+    for (int i = threadIdx.x; i < nsr * kTileB; i += blockDim.x) {
       Pstage[i] = Real(Pt[smap[i >> 3] * kTileB + (i & 7)]);
       if (project) Ps[i] = 0.0;
     }
@@ -264,7 +275,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   for (int k = 0; k < 9; ++k) sacc[k] = Real(0);
   const int nbx = g.nbr[0], nby = g.nbr[1];
 
-  for (int bi = warp; bi < nbx * nby; bi += kThreads / 32) {
+  for (int bi = warp; bi < nbx * nby; bi += nw) {
     const int bx = bi % nbx, by = bi / nbx;
     const int br = (slab * nby + by) * nbx + bx;
     const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
@@ -311,7 +322,9 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
           split_tf32(x1.x, ah[1], al[1]);
           split_tf32(x0.y, ah[2], al[2]);
           split_tf32(x1.y, ah[3], al[3]);
-          mma_tf32x3(acc[mt], ah, al, bh, bl);
+          mma_tf32(acc[mt], al, bh);   // small terms first
+          mma_tf32(acc[mt], ah, bl);
+          mma_tf32(acc[mt], ah, bh);
         }
       }
       Real* tw = tn_sm + warp * 16 * 32;
@@ -410,6 +423,8 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
         // next channel), K = 8 brick points per k-step, N = the 8 nodes.
         const int g8 = lane >> 2, t4 = lane & 3, ch = 2 * (g8 & 1);
         const Real* tw = tn_sm + warp * 16 * 32;
+        // one m-tile (4 images) per pass; separate accumulators for the three split terms
+        // measured slower (more registers live across the gather loads), so one chain
         for (int m4 = 0; m4 < nb; m4 += 4) {
           const int kr = m4 + (g8 >> 1);
           int4 r0 = make_int4(0, 0, 0, 0), r1 = make_int4(0, 0, 0, 0);
@@ -437,7 +452,9 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
             split_tf32(x1.y, ah[3], al[3]);
             split_tf32(float(tw[tn_index(8 * ks + t4, g8)]), bh[0], bl[0]);
             split_tf32(float(tw[tn_index(8 * ks + t4 + 4, g8)]), bh[1], bl[1]);
-            mma_tf32x3(d, ah, al, bh, bl);
+            mma_tf32(d, al, bh);
+            mma_tf32(d, ah, bl);
+            mma_tf32(d, ah, bh);
           }
           const int nch = r0.w & 0xff, prow = int(unsigned(r0.w) >> 16);
 #pragma unroll
@@ -490,17 +507,17 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     double sv = double(sacc[k]);
     sv += __shfl_xor_sync(0xffffffffu, sv, 8);
     sv += __shfl_xor_sync(0xffffffffu, sv, 16);
-    if (lane < kTileB) red[warp][lane][k] = sv;
+    if (lane < kTileB) red[(warp * kTileB + lane) * 9 + k] = sv;
   }
   __syncthreads();
-  for (int k2 = threadIdx.x; k2 < kTileB * 9; k2 += kThreads) {
+  for (int k2 = threadIdx.x; k2 < kTileB * 9; k2 += blockDim.x) {
     const int qq = k2 / 9, k = k2 % 9;
     double sv = 0.0;
-    for (int wv = 0; wv < kThreads / 32; ++wv) sv += red[wv][qq][k];
+    for (int wv = 0; wv < nw; ++wv) sv += red[(wv * kTileB + qq) * 9 + k];
     Spart[(((size_t)tl * g.nslab + slab) * kTileB + qq) * 9 + k] = sv;
   }
   if (kSmemP && project) {
-    for (int i = threadIdx.x; i < nsr * kTileB; i += kThreads) {
+    for (int i = threadIdx.x; i < nsr * kTileB; i += blockDim.x) {
       const double s = Ps[i];
       if (s != 0.0) atomicAdd(&Pn[smap[i >> 3] * kTileB + (i & 7)], s);
     }
@@ -577,21 +594,27 @@ k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restr
   for (int i = threadIdx.x; i < nr * B; i += kThreads) Pt[i] = 0.0;
 }
 
-constexpr int kStepSmemMax = 160 * 1024;   // dynamic shared memory of k_step with staged projections
+// dynamic shared memory of k_step: staged projections (at most kStepRowsSmemMax, else they stay
+// in global memory) + the per-warp arrays
+constexpr int kStepRowsSmemMax = 160 * 1024;
+constexpr int kStepSmemMax = kStepRowsSmemMax + (kStepThreads / 32) * (kTileB * 9 * 8 + 16 * 32 * 8);
 
 template <typename Real, int NO>
 static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
                        const double* Pg, double* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                        int mode) {
   const int rows_smem = int(smem / (kTileB * (sizeof(double) + sizeof(Real))));
-  if (smem <= kStepSmemMax) {
-    // the kernel also holds static shared arrays: always opt in. The attribute belongs to the
-    // function, not the launch, and handles on other host threads launch the same kernel, so
-    // every caller sets the same value (the largest dynamic size this path uses)
+  const int nw = step_warps(h->geo.nbr[0] * h->geo.nbr[1]), nthr = 32 * nw;
+  const size_t smem_warps = size_t(nw) * (kTileB * 9 * sizeof(double) + 16 * 32 * sizeof(Real));
+  // The dynamic-size attribute belongs to the function, not the launch, and handles on other
+  // host threads launch the same kernel, so every caller sets the same value (the largest
+  // dynamic size this kernel uses)
+  if (smem <= kStepRowsSmemMax) {
+    smem += smem_warps;
     if (sizeof(Real) == 4 && h->proj4) {
       SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, sizeof(Real) == 4>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmemMax));
-      k_step<Real, NO, true, sizeof(Real) == 4><<<grid, kThreads, smem, h->stream>>>(
+      k_step<Real, NO, true, sizeof(Real) == 4><<<grid, nthr, smem, h->stream>>>(
           h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n,
           v, h->d.scal, mode, h->wb.Spart, rows_smem);
       SQ_LAUNCH_CHECK(h);
@@ -599,11 +622,13 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
     }
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
-    k_step<Real, NO, true, false><<<grid, kThreads, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+    k_step<Real, NO, true, false><<<grid, nthr, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
                                                                 h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                                 h->d.scal, mode, h->wb.Spart, rows_smem);
   } else {
-    k_step<Real, NO, false, false><<<grid, kThreads, 0, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+    SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kStepSmemMax));
+    k_step<Real, NO, false, false><<<grid, nthr, smem_warps, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
                                                               h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                               h->d.scal, mode, h->wb.Spart, 0);
   }

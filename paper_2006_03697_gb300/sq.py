@@ -28,7 +28,7 @@ SQ_N_MOMENTS = 17
 
 EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
-    "sq_density_energy_stress_dev", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
+    "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
     "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit",
     "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_destroy", "sq_last_error",
 ]
@@ -86,6 +86,7 @@ def lib():
         L.sq_fermi_level.argtypes = [H, C.POINTER(C.c_double)]
         L.sq_density_energy_stress.argtypes = [H, C.c_double, C.c_void_p, C.POINTER(sq_energies), C.c_void_p]
         L.sq_density_energy_stress_dev.argtypes = [H, C.c_double, C.c_void_p, C.POINTER(sq_energies), C.c_void_p]
+        L.sq_pressure.argtypes = [H, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.sq_get_bounds.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.sq_moments_copy.argtypes = [H, C.c_void_p]
         L.sq_footprint_bytes.argtypes = [C.POINTER(sq_instance_desc)]
@@ -117,7 +118,7 @@ def lib():
         L.sq_last_error.argtypes = [H]
         L.sq_last_error.restype = C.c_char_p
         for name in ("sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
-                     "sq_density_energy_stress_dev", "sq_get_bounds", "sq_moments_copy"):
+                     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_moments_copy"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -207,6 +208,13 @@ def sq_density_energy_stress_dev(h, mu: float, rho_dev_ptr: int | None, sigma_de
     return {k: getattr(e, k) for k, _ in sq_energies._fields_} if energies else None
 
 
+def sq_pressure(h, mu: float):
+    """App. A pressure (kinetic + nonlocal terms), Ha/bohr^3, and E_pot (Ha)."""
+    p, ep = C.c_double(), C.c_double()
+    _check(lib().sq_pressure(h, C.c_double(mu), C.byref(p), C.byref(ep)), h)
+    return p.value, ep.value
+
+
 def sq_get_bounds(h):
     lo, hi = C.c_double(), C.c_double()
     _check(lib().sq_get_bounds(h, C.byref(lo), C.byref(hi)), h)
@@ -266,8 +274,9 @@ def run(inst: dict, precision=SQ_FP64, bounds=None, want_moments=False, stream=N
         mu = sq_fermi_level(h)
         nd = int(np.prod(inst["n"]))
         rho, en, sig = sq_density_energy_stress(h, mu, nd)
+        p_a, e_pot = sq_pressure(h, mu)
         out = {"mu": mu, "rho": rho, "sigma": sig, "bounds": sq_get_bounds(h),
-               "launches": sq_kernel_launches(h)}
+               "launches": sq_kernel_launches(h), "pressure_A": p_a, "E_pot": e_pot}
         out.update(en)
         if want_moments:
             out["moments"] = sq_moments_copy(h, nd, int(inst["n_pl"]))

@@ -31,11 +31,13 @@ def test_header_symbols_exported(sq):
 
 def test_footprint_scales_with_problem(sq):
     f1 = sq.sq_footprint_bytes(sq.Desc(make_instance(1), sq.SQ_FP64, bounds=(-1.0, 40.0)))
+    f1m = sq.sq_footprint_bytes(sq.Desc(make_instance(1), sq.SQ_MIXED, bounds=(-1.0, 40.0)))
     f2 = sq.sq_footprint_bytes(sq.Desc(make_instance(2), sq.SQ_FP64, bounds=(-1.0, 130.0)))
     f2m = sq.sq_footprint_bytes(sq.Desc(make_instance(2), sq.SQ_MIXED, bounds=(-1.0, 130.0)))
     assert 0 < f1 < f2
-    assert 0 < f2m <= f2
-    assert f2 < 64 << 30
+    assert 0 < f1m < f1            # one wave: FP32 vectors and tables take less room
+    # larger problems run in waves of at most 24 GiB of per-tile buffers
+    assert 0 < f2m < 32 << 30 and f2 < 32 << 30
 
 
 @pytest.mark.parametrize("field,value", [

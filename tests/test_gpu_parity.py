@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import sq_oracle as orc
-from workloads import make_instance, tiny_instance
+from workloads import make_batch, make_instance, tiny_instance
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def _check_moments(gpu, ref, rtol):
 
 def _check_results(g, o, rtol, nd):
     assert abs(g["mu"] - o["mu"]) <= rtol * max(1.0, abs(o["mu"]))
-    for key in ("E_band", "E_s", "E_nl", "N_check"):
+    for key in ("E_band", "E_s", "E_nl", "N_check", "E_pot", "pressure_A"):
         assert abs(g[key] - o[key]) <= rtol * max(1.0, abs(o[key])), key
     assert np.abs(g["rho"] - o["rho"]).max() <= rtol * np.abs(o["rho"]).max()
     assert np.abs(g["sigma"] - o["sigma"]).max() <= rtol * max(np.abs(o["sigma"]).max(), 1e-3)
@@ -94,6 +94,7 @@ def test_mixed_precision_config1(sq, config1_ref):
         assert abs(g[key] - o[key]) <= E_RTOL_MIXED * abs(o[key]) + 1e-9, key
     assert abs(g["F"] - o["F"]) <= E_RTOL_MIXED * abs(o["F"])
     assert np.abs(g["sigma"] - o["sigma"]).max() <= SIG_ATOL_MIXED
+    assert abs(g["pressure_A"] - o["pressure_A"]) <= SIG_ATOL_MIXED
     assert abs(g["mu"] - o["mu"]) <= 1e-5 * max(1.0, abs(o["mu"]))
     assert np.abs(g["rho"] - o["rho"]).max() <= 1e-4 * np.abs(o["rho"]).max()
 
@@ -140,6 +141,51 @@ def test_config2_sampled_nodes_and_invariants(sq, config2_setup, precision):
     assert abs(en["N_check"] - inst["n_e"]) <= 1e-9 * inst["n_e"]
     assert np.all(np.isfinite(sig)) and np.all(rho > 0.0)
     assert np.all(np.diag(sig) < 0.0)
+
+
+@pytest.fixture(scope="module")
+def config4_large_setup():
+    # 32 H on a 32^3 grid (9.6 bohr), R_cut 4.80 -> m = 16: 33^3 regions, the largest window of
+    # the batched snapshots; n_pl = 73, kT = 2.25 (the coldest of the sampled snapshots)
+    inst = make_batch(4, count=31, atom_choices=(32,))[30]
+    prob = orc.Problem(inst)
+    assert list(prob.m) == [16, 16, 16] and prob.n_pl == 73
+    # given bounds that contain every H_q spectrum (the oracle's Lanczos gives (-1.29, 119.6)
+    # here, but takes minutes at m = 16)
+    bounds = (-5.0, 125.0)
+    nodes = [0, 5000, 17000, 32 ** 3 - 1]
+    ref = orc.all_moments(prob, *bounds, nodes=nodes, workers=2)
+    return inst, bounds, nodes, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config4_largest_window_sampled_nodes(sq, config4_large_setup, precision):
+    """m = 16 (union window 34, padded to 36 in x: 9 x 9 bricks per slab with a ragged last
+    brick in y and z, 7 warps for 81 bricks), n_pl = 73: sampled moment rows (FP64) and the
+    density at test-chosen mu (both modes) against the oracle, electron count at the Fermi level."""
+    inst, bounds, nodes, ref = config4_large_setup
+    nd = 32 ** 3
+    mode = sq.SQ_FP64 if precision == "fp64" else sq.SQ_MIXED
+    h = sq.sq_setup(sq.Desc(inst, mode, bounds=bounds))
+    try:
+        sq.sq_moments(h)
+        if precision == "fp64":
+            mom = sq.sq_moments_copy(h, nd, 73)
+            _check_moments(mom[nodes], ref, RTOL64)
+        prob = orc.Problem(inst)
+        for mu in (-9.0, -8.0):
+            rho, en, sig = sq.sq_density_energy_stress(h, mu, nd)
+            c, _, _ = orc.fd_coefficients(mu, prob.kT, 0.5 * (bounds[1] + bounds[0]), 0.5 * (bounds[1] - bounds[0]),
+                                          prob.n_pl, prob.M)
+            rho_ref = 2.0 / prob.dV * (ref[:, :, 0] @ (orc.primed(prob.n_pl) * c))
+            tol = RTOL64 if precision == "fp64" else 2e-5
+            assert np.abs(rho[nodes] - rho_ref).max() <= tol * np.abs(rho_ref).max()
+        mu = sq.sq_fermi_level(h)
+        rho, en, sig = sq.sq_density_energy_stress(h, mu, nd)
+    finally:
+        sq.sq_destroy(h)
+    assert abs(en["N_check"] - inst["n_e"]) <= 1e-9 * inst["n_e"]
+    assert np.all(np.isfinite(sig)) and np.all(np.diag(sig) < 0.0)
 
 
 def test_call_order_errors(sq):

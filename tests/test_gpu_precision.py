@@ -29,9 +29,10 @@ def sq():
 
 def _table(name, mixed, ref):
     rows = [f"precision {name}: mixed vs reference"]
-    for key in ("E_band", "E_s", "E_nl", "F", "mu"):
+    for key in ("E_band", "E_s", "E_nl", "F", "mu", "E_pot"):
         rel = abs(mixed[key] - ref[key]) / max(1e-300, abs(ref[key]))
         rows.append(f"  {key:7s} {ref[key]: .12e}  rel err {rel:.2e}")
+    rows.append(f"  P (App. A) {ref['pressure_A']: .12e}  abs err {abs(mixed['pressure_A'] - ref['pressure_A']):.2e}")
     drho = np.abs(mixed["rho"] - ref["rho"]).max() / np.abs(ref["rho"]).max()
     rows.append(f"  rho     max rel err {drho:.2e}")
     ds = np.abs(np.asarray(mixed["sigma"]) - np.asarray(ref["sigma"]))
@@ -46,6 +47,7 @@ def _check(mixed, ref, ds):
         assert abs(mixed[key] - ref[key]) <= 1e-6 * abs(ref[key]), key
     assert abs(mixed["E_nl"] - ref["E_nl"]) <= 1e-6 * abs(ref["E_band"])
     assert ds.max() <= 1e-5
+    assert abs(mixed["pressure_A"] - ref["pressure_A"]) <= 1e-5
 
 
 def test_precision_config1_vs_oracle(sq):
