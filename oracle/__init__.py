@@ -13,4 +13,5 @@ Modules
                 Mermin free energy under homogeneous strain, Eq. (stressdefinition))
   free_electron closed forms for V_eff = 0 and no projectors (Brillouin-zone integrals
                 and the exactly separable truncated region)
+  green_kubo    Green-Kubo shear viscosity of a stress time series (Eq. viscosity)
 """

@@ -11,7 +11,7 @@ import pytest
 import scipy.integrate
 import scipy.linalg
 
-from oracle import dense_k, free_electron
+from oracle import dense_k, free_electron, green_kubo
 from oracle.sq_oracle import (K_PAIRS, NodeRegion, Problem, cheb_coeffs, chebyshev_columns, contract,
                               entropy_fn, fd_coefficients, fd_weights, fermi, fermi_bisect, lanczos_bounds,
                               node_moments, primed, run)
@@ -397,3 +397,68 @@ def test_p10_pressure_equals_trace_stress_with_second_difference_kinetic_term():
         diffs.append(abs(out["pressure_A"] - p_trace))
     assert diffs[1] < 1e-12 * abs(out["pressure_A"])
     assert diffs[0] > diffs[1]
+
+
+# ---------------------------------------------------------------- P11: Green-Kubo viscosity
+def _sigma_series(s12):
+    """(n_traj, n_steps, 3, 3) stress tensors with only sigma_12 = sigma_21 non-zero."""
+    sig = np.zeros(s12.shape + (3, 3))
+    sig[..., 0, 1] = s12
+    sig[..., 1, 0] = s12
+    return sig
+
+
+def test_p11_green_kubo_cosine_closed_form():
+    """s_12(t) = A cos(w t): the origin-averaged autocorrelation has the closed form
+    (A^2/5) [cos(w k)/2 + sin(w K) cos(w (k + K - 1)) / (2 K sin w)], K = n - k origins
+    (product-to-sum and the geometric sum of cosines); eta is |Omega|/kT times its trapezoid."""
+    n, A, w, dt, vol, kT = 400, 0.03, 0.173, 2.5, 1728.0, 3.17
+    t = np.arange(n)
+    sig = _sigma_series((A * np.cos(w * t))[None, :])
+    eta, c = green_kubo.viscosity(sig, dt, vol, kT, 60)
+    k = np.arange(61)
+    K = n - k
+    closed = A * A / 5.0 * (0.5 * np.cos(w * k) + np.sin(w * K) * np.cos(w * (k + K - 1)) / (2.0 * K * np.sin(w)))
+    np.testing.assert_allclose(c, closed, rtol=0, atol=1e-15)
+    trap = np.concatenate([[0.0], np.cumsum(0.5 * dt * (closed[:-1] + closed[1:]))])
+    np.testing.assert_allclose(eta, vol / kT * trap, rtol=1e-12, atol=0)
+
+
+def test_p11_green_kubo_deviatoric_invariance_and_component_weights():
+    """An isotropic pressure p(t) I added to sigma leaves the viscosity unchanged (only the
+    traceless part enters); sigma_11 = -sigma_22 = x(t) enters through (s_11 - s_22)/2 and
+    (s_22 - s_33)/2 with weights 1 and 1/4 of x, against 1 for x in sigma_12."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    sig = rng.normal(size=(2, 300, 3, 3)) * 0.01
+    sig = 0.5 * (sig + np.swapaxes(sig, -1, -2))
+    eta0, _ = green_kubo.viscosity(sig, 1.0, 1000.0, 2.0, 40)
+    p = rng.normal(size=(2, 300)) * 5.0
+    eta1, _ = green_kubo.viscosity(sig + p[..., None, None] * np.eye(3), 1.0, 1000.0, 2.0, 40)
+    np.testing.assert_allclose(eta1, eta0, rtol=1e-9, atol=1e-12)
+    x = rng.normal(size=(1, 500))
+    s_shear = _sigma_series(x)
+    s_normal = np.zeros_like(s_shear)
+    s_normal[..., 0, 0] = x
+    s_normal[..., 1, 1] = -x
+    c_shear = green_kubo.stress_acf(s_shear, 5)
+    c_normal = green_kubo.stress_acf(s_normal, 5)
+    np.testing.assert_allclose(c_normal, c_shear * (1.0 + 0.25), rtol=1e-12)
+
+
+def test_p11_green_kubo_exponential_correlation():
+    """An Ornstein-Uhlenbeck sigma_12 with unit variance and correlation time tau (steps):
+    C(k) -> exp(-k / tau) / 5 and eta(inf) -> (|Omega|/kT) dt (1/5) (1 + e^{-1/tau}) / (2 (1 - e^{-1/tau}))
+    (the trapezoid sum of the exponential), within the statistical error of 4 x 200k steps."""
+    tau, n, ntr = 8.0, 200_000, 4
+    a = math.exp(-1.0 / tau)
+    rng = np.random.Generator(np.random.PCG64(5))
+    x = np.empty((ntr, n))
+    x[:, 0] = rng.normal(size=ntr)
+    noise = rng.normal(size=(ntr, n)) * math.sqrt(1.0 - a * a)
+    for i in range(1, n):
+        x[:, i] = a * x[:, i - 1] + noise[:, i]
+    dt, vol, kT = 0.5, 100.0, 1.0
+    eta, c = green_kubo.viscosity(_sigma_series(x), dt, vol, kT, 80)
+    np.testing.assert_allclose(c[:4], np.exp(-np.arange(4) / tau) / 5.0, atol=0.01)
+    expect = vol / kT * dt / 5.0 * 0.5 * (1.0 + a) / (1.0 - a)
+    assert abs(eta[-1] - expect) < 0.1 * expect
