@@ -241,6 +241,23 @@ int sq_server_pending(sq_server* s);
  * polled are dropped). */
 void sq_server_destroy(sq_server* s);
 
+/* Green-Kubo shear viscosity (Sec. 5.2, Eq. viscosity) of a stress time series, e.g. the sigma
+ * of successive snapshots of a trajectory served through sq_server_*:
+ *   eta(k dt) = |Omega| / kT * int_0^{k dt} (1/5) sum_i <s_i(t') s_i(0)> dt',
+ *   s_i = sigma_12, sigma_23, sigma_31, (sigma_11 - sigma_22)/2, (sigma_22 - sigma_33)/2.
+ * <s_i(k dt) s_i(0)> is the mean of s_i(t + k) s_i(t) over every time origin t = 0..n_steps-1-k
+ * of every trajectory (independent initial conditions); the integral is the trapezoid rule.
+ * sigma_host: [n_traj][n_steps][9] row-major 3 x 3 stresses (Ha/bohr^3), host memory, not
+ * retained. dt: sampling interval (atomic time units, 2.4189e-17 s); volume |Omega| (bohr^3);
+ * kT (Ha). Outputs (host): eta_out [max_lag + 1] in atomic units (1 = 0.7117 mPa s),
+ * acf_out [max_lag + 1] (Ha^2/bohr^6) or NULL. Runs on the current device on stream (NULL =
+ * default) with scratch it allocates and frees; synchronises the stream. Deterministic.
+ * Errors: SQ_ERR_INVALID_ARG (NULL sigma_host / eta_out, n_traj < 1, n_steps < 2,
+ * max_lag outside [0, n_steps), non-positive dt, volume or kT), SQ_ERR_OOM, SQ_ERR_CUDA; the
+ * text is in sq_last_error(NULL). */
+int sq_green_kubo(const double* sigma_host, int n_traj, int n_steps, double dt, double volume, double kT,
+                  int max_lag, void* stream, double* eta_out, double* acf_out);
+
 void sq_destroy(sq_handle* h);
 
 /* Last error text of h (or of the last failed sq_setup when h is NULL); never NULL. */

@@ -235,7 +235,9 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   int M = d->cheb_quad_M > 0 ? d->cheb_quad_M : 2048;
   P.fixed_bytes = size_t(Nd) * (sizeof(double) + sizeof(float)) +                       // V
                   P.atoms.size() * sizeof(sq::AtomTab) + size_t(ch) * 6 * sizeof(double) +
-                  size_t(P.table_len) * real +
+                  // projector tables: FP64 (always; the Lanczos apply and the FP64 sweep), FP32 and
+                  // TF32 hi/lo pairs for the mixed sweep
+                  size_t(P.table_len) * (sizeof(double) + (real == sizeof(float) ? 3 * sizeof(float) : 0)) +
                   size_t(Nd) * size_t(d->n_pl + 1) * SQ_N_MOMENTS * sizeof(double) +   // moments
                   size_t(d->n_pl + 1) * 4 * sizeof(double) + size_t(M) * sizeof(double) +
                   size_t(Nd) * sizeof(double) + 4096 * 32 * sizeof(double) + 1024;
@@ -264,7 +266,6 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
     const size_t nst = P.lz_tiles.size();
     P.fixed_bytes += sizeof(double) * (size_t(k + 2) * nst * g.Upts * g.B + nst * size_t(g.r_cap) * g.B +
                                        nst * g.B * size_t(5 * k + 8)) + sizeof(int) * nst;
-    P.fixed_bytes += sizeof(double) * size_t(P.table_len);   // FP64 tables for the Lanczos apply
   }
   // tiles per wave: keep the per-wave working set under 24 GiB (fewer, larger launches: less
   // per-wave setup and a smaller tail), with the tiles spread evenly over the waves
@@ -442,6 +443,7 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->d.gdv32, sizeof(float) * std::max(1, h->n_ch_total));
   SQ_ALLOC(h->d.chi64, sizeof(double) * std::max<long long>(1, P.table_len));
   if (!f64) SQ_ALLOC(h->d.chi32, sizeof(float) * std::max<long long>(1, P.table_len));
+  if (!f64) SQ_ALLOC(h->d.chi32s, 2 * sizeof(float) * std::max<long long>(1, P.table_len));
   SQ_ALLOC(h->d.mom, sizeof(double) * size_t(Nd) * size_t(g.n_pl + 1) * SQ_N_MOMENTS);
   SQ_ALLOC(h->d.R, sizeof(double) * (g.n_pl + 1));
   SQ_ALLOC(h->d.cosF, sizeof(double) * h->M);

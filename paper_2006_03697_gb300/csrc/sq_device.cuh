@@ -35,6 +35,13 @@ __device__ __forceinline__ bool in_window(const Geo& g, const int qo[3], int ux,
          (unsigned)(uz - qo[2]) <= (unsigned)(2 * g.m[2]);
 }
 
+// x = hi + lo with hi, lo TF32 values (11 significant bits each, held in FP32 registers)
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
 // Linear index of an absolute lattice point inside an atom image's support box, or -1.
 __device__ __forceinline__ int box_index(const AtomTab& at, const int s[3], const int n[3],
                                          int ax, int ay, int az) {

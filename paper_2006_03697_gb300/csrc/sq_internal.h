@@ -122,6 +122,7 @@ struct Dev {
   float* gdv32 = nullptr;
   double* chi64 = nullptr;        // projector tables
   float* chi32 = nullptr;
+  float* chi32s = nullptr;        // mixed: each FP32 table value as a TF32 (hi, lo) pair
   double* mom = nullptr;          // [N_d][n_pl+1][17]
   double* R = nullptr;            // [n_pl+1] node sums of rho^j
   double* cosF = nullptr;         // [M] sum'_j cos(j theta_k) R^j

@@ -35,6 +35,17 @@ __global__ void k_chi_tables(Geo g, const AtomTab* __restrict__ atoms, const dou
   }
 }
 
+// out[2 i], out[2 i + 1] = TF32 (hi, lo) of in[i]: the tensor-core projector phases load a
+// point's channel pair as one 16-byte (hi, lo, hi, lo) group
+__global__ void k_split_tf32(const float* __restrict__ in, long long n, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    uint32_t hi, lo;
+    split_tf32(in[i], hi, lo);
+    out[2 * i] = __uint_as_float(hi);
+    out[2 * i + 1] = __uint_as_float(lo);
+  }
+}
+
 // One block per tile of the wave: list the atom images (atom, shift s) whose support box
 // meets the tile's union window, atom-major then s (x fastest); assign projector rows.
 __global__ void k_tile_entries(Geo g, Wave w, const AtomTab* __restrict__ atoms, TileEntry* __restrict__ entries,
@@ -351,6 +362,8 @@ int build_tables(sq_handle* h) {
   SQ_LAUNCH_CHECK(h);
   if (h->precision == SQ_MIXED) {
     k_chi_tables<float><<<h->geo.n_atoms, 256, 0, h->stream>>>(h->geo, h->d.atoms, h->d.gdv, h->d.chi32);
+    SQ_LAUNCH_CHECK(h);
+    k_split_tf32<<<1024, 256, 0, h->stream>>>(h->d.chi32, h->table_len, h->d.chi32s);
     SQ_LAUNCH_CHECK(h);
   }
   return SQ_OK;

@@ -163,11 +163,6 @@ constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x
 // ---- warp-level TF32 tensor-core products for the FP32 projector phases.
 // x = hi + lo with hi, lo TF32 (11 significant bits each); a product is taken as
 // hi*hi + hi*lo + lo*hi with FP32 accumulation (the lo*lo term, ~2^-22 relative, is dropped).
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-  const float r = x - __uint_as_float(hi);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
-}
 
 // d (16 x 8, FP32) += a (16 x 8, TF32, row) * b (8 x 8, TF32, col); fragment of lane (g, t),
 // g = lane / 4, t = lane % 4: a = {(g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4)},
@@ -178,6 +173,8 @@ __device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], const 
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
+
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
 // the brick's t values in the per-warp shared array: point p = a + 4 b + 16 c, node q
 __device__ __forceinline__ int tn_index(int p, int q) { return (p >> 2) * 32 + (p & 3) * kTileB + q; }
@@ -208,8 +205,8 @@ template <typename Real, int NO, bool kSmemP, bool kMMA>
 __global__ void __launch_bounds__(kStepThreads, sizeof(Real) == 4 ? 3 : 2)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
        const double* __restrict__ Pg, double* __restrict__ Pg_next, const Real* __restrict__ Wt,
-       const Real* __restrict__ chi, const Real* __restrict__ gdv, const int4* __restrict__ brec,
-       const int* __restrict__ slab_n, const int* __restrict__ slab_map, const int* __restrict__ bn,
+       const Real* __restrict__ chi, const float* __restrict__ chis, const Real* __restrict__ gdv,
+       const int4* __restrict__ brec, const int* __restrict__ slab_n, const int* __restrict__ slab_map, const int* __restrict__ bn,
        const Real* __restrict__ v, const double* __restrict__ scal, int mode, double* __restrict__ Spart,
        int rows_smem) {
   // dynamic shared memory: [Ps: rows_smem x 8 FP64][red: nw x 8 x 9 FP64][Pstage: rows_smem x 8]
@@ -270,9 +267,27 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   const bool valid = node_valid(g, o, qo);
   const Real* Wq = Wt + (size_t)tl * 3 * g.Upts * kTileB;
   const size_t wstr = (size_t)g.Upts * kTileB;
+  // S partial sums: per lane across bricks (scalar path); the paired phase B reduces them per
+  // brick over its point lanes into a per-warp FP32 array (red, read as floats), so no S
+  // registers stay live through the projector phases
   Real sacc[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) sacc[k] = Real(0);
+  float* red32 = reinterpret_cast<float*>(red) + warp * kTileB * 9;
+  if constexpr (kMMA) {
+    for (int k = lane; k < kTileB * 9; k += 32) red32[k] = 0.f;
+    __syncwarp();
+  }
+  // paired phase B: lane = node pair np2 (nodes 2 np2, 2 np2 + 1: x offsets 0 and 1), x-point xa2,
+  // y parity yb2
+  const int np2 = lane & 3, xa2 = (lane >> 2) & 3, yb2 = lane >> 4;
+  const int qo2[3] = {0, np2 & 1, np2 >> 1};
+  bool valid2[2];
+  {
+    int qa[3] = {0, qo2[1], qo2[2]}, qb[3] = {1, qo2[1], qo2[2]};
+    valid2[0] = node_valid(g, o, qa);
+    valid2[1] = node_valid(g, o, qb);
+  }
   const int nbx = g.nbr[0], nby = g.nbr[1];
 
   for (int bi = warp; bi < nbx * nby; bi += nw) {
@@ -308,20 +323,17 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
         split_tf32(p0, bh[0], bl[0]);
         split_tf32(p1, bh[1], bl[1]);
         const int dx = r1.x, plane = r1.x * r1.y * 4;
-        const float* xb = reinterpret_cast<const float*>(chi) + r0.x + (pb0 * dx + pa0) * 4 + ch;
+        // (hi, lo) pairs of channels ch, ch + 1 at point (pa0, pb0, 0): one 16-byte load per point
+        const float* xb = chis + 2 * (r0.x + (pb0 * dx + pa0) * 4 + ch);
         const unsigned mlo = unsigned(r1.z) >> g8, mhi = unsigned(r1.w) >> g8;
 #pragma unroll
         for (int mt = 0; mt < 4; ++mt) {
           const unsigned mw = (mt < 2) ? mlo : mhi;
           const int sh = 16 * (mt & 1);
-          float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
-          if ((mw >> sh) & 1u) x0 = *reinterpret_cast<const float2*>(xb + mt * plane);
-          if ((mw >> (sh + 8)) & 1u) x1 = *reinterpret_cast<const float2*>(xb + mt * plane + 8 * dx);
-          uint32_t ah[4], al[4];
-          split_tf32(x0.x, ah[0], al[0]);
-          split_tf32(x1.x, ah[1], al[1]);
-          split_tf32(x0.y, ah[2], al[2]);
-          split_tf32(x1.y, ah[3], al[3]);
+          uint4 x0 = make_uint4(0u, 0u, 0u, 0u), x1 = make_uint4(0u, 0u, 0u, 0u);
+          if ((mw >> sh) & 1u) x0 = *reinterpret_cast<const uint4*>(xb + 2 * mt * plane);
+          if ((mw >> (sh + 8)) & 1u) x1 = *reinterpret_cast<const uint4*>(xb + 2 * (mt * plane + 8 * dx));
+          const uint32_t ah[4] = {x0.x, x1.x, x0.z, x1.z}, al[4] = {x0.y, x1.y, x0.w, x1.w};
           mma_tf32(acc[mt], al, bh);   // small terms first
           mma_tf32(acc[mt], ah, bl);
           mma_tf32(acc[mt], ah, bh);
@@ -366,49 +378,125 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
       }
     }
     __syncwarp();
+    if constexpr (kMMA) {
+      // phase B with two nodes per lane: lane = (node pair np, x-point xa, y parity yb); iteration
+      // it covers brick points (xa, 2 (it % 2) + yb, it / 2) for nodes 2 np and 2 np + 1, so every
+      // t / W load is an 8-byte pair and a brick takes 8 iterations (half the load round trips)
+      Real* tw = tn_sm + warp * 16 * 32;
+      float sb[18];   // S partials of nodes 2 np2 and 2 np2 + 1 over this brick
+#pragma unroll
+      for (int k = 0; k < 18; ++k) sb[k] = 0.f;
 #pragma unroll 1
-    for (int it = 0; it < 16; ++it) {
-      const int pb = it & 3, pc = it >> 2;
-      const int ux = bx * kBrick + pa, uy = by * kBrick + pb, uz = slab * kBrick + pc;
-      const bool inU = (uy < Uy) && (uz < Uz);
-      const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + q;
-      const bool inwin = inU && valid && in_window(g, qo, ux, uy, uz);
-      Real tn = Real(0);
-      if (inwin) {
-        // loads that do not depend on the stencil, issued first
-        const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
-        const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
-        const Real tc = T[e];
-        Real y = Real(0);                           // off-diagonal part of H t^j
-        Real gr[3];
-        const int u[3] = {ux, uy, uz};
+      for (int it = 0; it < 8; ++it) {
+        const int pb = 2 * (it & 1) + yb2, pc = it >> 1;
+        const int ux = bx * kBrick + xa2, uy = by * kBrick + pb, uz = slab * kBrick + pc;
+        const int p = xa2 + 4 * pb + 16 * pc;
+        const bool inU = (uy < Uy) && (uz < Uz);
+        const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + 2 * np2;
+        const bool inyz = inU && (unsigned)(uy - qo2[1]) <= (unsigned)(2 * g.m[1]) &&
+                          (unsigned)(uz - qo2[2]) <= (unsigned)(2 * g.m[2]);
+        const bool in0 = inyz && valid2[0] && (unsigned)ux <= (unsigned)(2 * g.m[0]);
+        const bool in1 = inyz && valid2[1] && (unsigned)(ux - 1) <= (unsigned)(2 * g.m[0]);
+        float2 tn = make_float2(0.f, 0.f);
+        if (in0 || in1) {
+          const float2 w0 = ld2(Wq + e), w1 = ld2(Wq + wstr + e), w2 = ld2(Wq + 2 * wstr + e);
+          const float2 tp = (mode == 1) ? ld2(Tp + tbase + e) : make_float2(0.f, 0.f);
+          const float2 tc = ld2(T + e);
+          float2 y = make_float2(0.f, 0.f);           // off-diagonal part of H t^j
+          float2 gr[3];
+          const int u[3] = {ux, uy, uz};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          gr[a] = Real(0);
+          for (int a = 0; a < 3; ++a) {
+            gr[a] = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int pp = 1; pp <= NO; ++pp) {
-            const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
-            const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
-            y += Coef<Real>::lap(g, a, pp) * (fp + fm);
-            gr[a] += Coef<Real>::grd(g, a, pp) * (fp - fm);
+            for (int pp = 1; pp <= NO; ++pp) {
+              const float2 fp = (u[a] + pp < Ua[a]) ? ld2(T + e + (size_t)pp * st[a]) : make_float2(0.f, 0.f);
+              const float2 fm = (u[a] - pp >= 0) ? ld2(T + e - (size_t)pp * st[a]) : make_float2(0.f, 0.f);
+              const float wl = Coef<float>::lap(g, a, pp), wg = Coef<float>::grd(g, a, pp);
+              y.x += wl * (fp.x + fm.x);
+              y.y += wl * (fp.y + fm.y);
+              gr[a].x += wg * (fp.x - fm.x);
+              gr[a].y += wg * (fp.y - fm.y);
+            }
           }
-        }
-        const Real vloc = v[wrz[uz - slab * kBrick] + wry[uy] + wrx[ux]];   // V_eff at the wrapped node
-        y += tnv[it * 32];                          // nonlocal part from phase A
-        if (mode != 2) {
-          tn = ca * y + (cd + ca * vloc) * tc - cc * tp;
-          Tn[tbase + e] = tn;
-        }
+          const float vloc = float(v[wrz[uz - slab * kBrick] + wry[uy] + wrx[ux]]);
+          const float2 ynl = *reinterpret_cast<const float2*>(tw + tn_index(p, 2 * np2));   // phase A
+          y.x += ynl.x;
+          y.y += ynl.y;
+          if (mode != 2) {
+            const float dg = float(cd) + float(ca) * vloc;
+            if (in0) tn.x = float(ca) * y.x + dg * tc.x - float(cc) * tp.x;
+            if (in1) tn.y = float(ca) * y.y + dg * tc.y - float(cc) * tp.y;
+            *reinterpret_cast<float2*>(Tn + tbase + e) = tn;
+          }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          sacc[3 * a + 0] += gr[a] * w0;
-          sacc[3 * a + 1] += gr[a] * w1;
-          sacc[3 * a + 2] += gr[a] * w2;
+          for (int a = 0; a < 3; ++a) {   // W is zero outside each node's window
+            sb[3 * a + 0] += gr[a].x * w0.x;
+            sb[3 * a + 1] += gr[a].x * w1.x;
+            sb[3 * a + 2] += gr[a].x * w2.x;
+            sb[9 + 3 * a + 0] += gr[a].y * w0.y;
+            sb[9 + 3 * a + 1] += gr[a].y * w1.y;
+            sb[9 + 3 * a + 2] += gr[a].y * w2.y;
+          }
+        } else if (inU && mode != 2) {
+          *reinterpret_cast<float2*>(Tn + tbase + e) = tn;
         }
-      } else if (inU && mode != 2) {
-        Tn[tbase + e] = Real(0);
+        *reinterpret_cast<float2*>(tw + tn_index(p, 2 * np2)) = tn;
       }
-      tnv[it * 32] = tn;
+      // the brick's S partials: sum over the 8 point lanes of each node pair, lanes 0..3 add
+#pragma unroll
+      for (int k = 0; k < 18; ++k) {
+        float sv = sb[k];
+        sv += __shfl_xor_sync(0xffffffffu, sv, 4);
+        sv += __shfl_xor_sync(0xffffffffu, sv, 8);
+        sv += __shfl_xor_sync(0xffffffffu, sv, 16);
+        if (lane < 4) red32[(2 * lane + k / 9) * 9 + k % 9] += sv;
+      }
+    } else {
+#pragma unroll 1
+      for (int it = 0; it < 16; ++it) {
+        const int pb = it & 3, pc = it >> 2;
+        const int ux = bx * kBrick + pa, uy = by * kBrick + pb, uz = slab * kBrick + pc;
+        const bool inU = (uy < Uy) && (uz < Uz);
+        const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + q;
+        const bool inwin = inU && valid && in_window(g, qo, ux, uy, uz);
+        Real tn = Real(0);
+        if (inwin) {
+          // loads that do not depend on the stencil, issued first
+          const Real w0 = Wq[e], w1 = Wq[wstr + e], w2 = Wq[2 * wstr + e];
+          const Real tp = (mode == 1) ? Tp[tbase + e] : Real(0);
+          const Real tc = T[e];
+          Real y = Real(0);                           // off-diagonal part of H t^j
+          Real gr[3];
+          const int u[3] = {ux, uy, uz};
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            gr[a] = Real(0);
+#pragma unroll
+            for (int pp = 1; pp <= NO; ++pp) {
+              const Real fp = (u[a] + pp < Ua[a]) ? T[e + (size_t)pp * st[a]] : Real(0);
+              const Real fm = (u[a] - pp >= 0) ? T[e - (size_t)pp * st[a]] : Real(0);
+              y += Coef<Real>::lap(g, a, pp) * (fp + fm);
+              gr[a] += Coef<Real>::grd(g, a, pp) * (fp - fm);
+            }
+          }
+          const Real vloc = v[wrz[uz - slab * kBrick] + wry[uy] + wrx[ux]];   // V_eff at the wrapped node
+          y += tnv[it * 32];                          // nonlocal part from phase A
+          if (mode != 2) {
+            tn = ca * y + (cd + ca * vloc) * tc - cc * tp;
+            Tn[tbase + e] = tn;
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            sacc[3 * a + 0] += gr[a] * w0;
+            sacc[3 * a + 1] += gr[a] * w1;
+            sacc[3 * a + 2] += gr[a] * w2;
+          }
+        } else if (inU && mode != 2) {
+          Tn[tbase + e] = Real(0);
+        }
+        tnv[it * 32] = tn;
+      }
     }
     __syncwarp();
     // projections of t^{j+1} over this brick: each lane sums its 16 points in registers, a
@@ -433,7 +521,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
             r1 = rb[2 * kr + 1];
           }
           const int dx = r1.x, dy = r1.y;
-          const float* xb = reinterpret_cast<const float*>(chi) + r0.x + t4 * 4 + ch;   // point (t4, 0, 0)
+          const float* xb = chis + 2 * (r0.x + t4 * 4 + ch);   // (hi, lo) pairs at point (t4, 0, 0)
           const unsigned mlo = unsigned(r1.z) >> t4, mhi = unsigned(r1.w) >> t4;
           float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -441,15 +529,12 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
             // points p0 = 8 ks + t4 = (t4, 2 (ks % 2), ks / 2) and p1 = p0 + 4 (one row further in b)
             const unsigned mw = (ks < 4) ? mlo : mhi;
             const int sh = 8 * (ks & 3);
-            const float* xp = xb + ((ks >> 1) * dy + 2 * (ks & 1)) * dx * 4;
-            float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
-            if ((mw >> sh) & 1u) x0 = *reinterpret_cast<const float2*>(xp);
-            if ((mw >> (sh + 4)) & 1u) x1 = *reinterpret_cast<const float2*>(xp + dx * 4);
-            uint32_t ah[4], al[4], bh[2], bl[2];
-            split_tf32(x0.x, ah[0], al[0]);
-            split_tf32(x0.y, ah[1], al[1]);
-            split_tf32(x1.x, ah[2], al[2]);
-            split_tf32(x1.y, ah[3], al[3]);
+            const float* xp = xb + 2 * ((ks >> 1) * dy + 2 * (ks & 1)) * dx * 4;
+            uint4 x0 = make_uint4(0u, 0u, 0u, 0u), x1 = make_uint4(0u, 0u, 0u, 0u);
+            if ((mw >> sh) & 1u) x0 = *reinterpret_cast<const uint4*>(xp);
+            if ((mw >> (sh + 4)) & 1u) x1 = *reinterpret_cast<const uint4*>(xp + 2 * dx * 4);
+            const uint32_t ah[4] = {x0.x, x0.z, x1.x, x1.z}, al[4] = {x0.y, x0.w, x1.y, x1.w};
+            uint32_t bh[2], bl[2];
             split_tf32(float(tw[tn_index(8 * ks + t4, g8)]), bh[0], bl[0]);
             split_tf32(float(tw[tn_index(8 * ks + t4 + 4, g8)]), bh[1], bl[1]);
             mma_tf32(d, al, bh);
@@ -501,19 +586,23 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
       }
     }
   }
-  // S partials: fixed-order reduction per node (the 4 point lanes by shuffles, then warps)
+  // S partials: fixed-order reduction per node (the point lanes by shuffles, then warps)
+  if constexpr (!kMMA) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    double sv = double(sacc[k]);
-    sv += __shfl_xor_sync(0xffffffffu, sv, 8);
-    sv += __shfl_xor_sync(0xffffffffu, sv, 16);
-    if (lane < kTileB) red[(warp * kTileB + lane) * 9 + k] = sv;
+    for (int k = 0; k < 9; ++k) {
+      double sv = double(sacc[k]);
+      sv += __shfl_xor_sync(0xffffffffu, sv, 8);
+      sv += __shfl_xor_sync(0xffffffffu, sv, 16);
+      if (lane < kTileB) red[(warp * kTileB + lane) * 9 + k] = sv;
+    }
   }
   __syncthreads();
   for (int k2 = threadIdx.x; k2 < kTileB * 9; k2 += blockDim.x) {
     const int qq = k2 / 9, k = k2 % 9;
     double sv = 0.0;
-    for (int wv = 0; wv < nw; ++wv) sv += red[(wv * kTileB + qq) * 9 + k];
+    for (int wv = 0; wv < nw; ++wv)
+      sv += kMMA ? double(reinterpret_cast<const float*>(red)[(wv * kTileB + qq) * 9 + k])
+                 : red[(wv * kTileB + qq) * 9 + k];
     Spart[(((size_t)tl * g.nslab + slab) * kTileB + qq) * 9 + k] = sv;
   }
   if (kSmemP && project) {
@@ -615,20 +704,20 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
       SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, sizeof(Real) == 4>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmemMax));
       k_step<Real, NO, true, sizeof(Real) == 4><<<grid, nthr, smem, h->stream>>>(
-          h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n,
+          h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.chi32s, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n,
           v, h->d.scal, mode, h->wb.Spart, rows_smem);
       SQ_LAUNCH_CHECK(h);
       return SQ_OK;
     }
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
-    k_step<Real, NO, true, false><<<grid, nthr, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+    k_step<Real, NO, true, false><<<grid, nthr, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
                                                                 h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                                 h->d.scal, mode, h->wb.Spart, rows_smem);
   } else {
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
-    k_step<Real, NO, false, false><<<grid, nthr, smem_warps, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, gdv,
+    k_step<Real, NO, false, false><<<grid, nthr, smem_warps, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
                                                               h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                               h->d.scal, mode, h->wb.Spart, 0);
   }

@@ -30,7 +30,7 @@ EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
     "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit",
-    "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_destroy", "sq_last_error",
+    "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_green_kubo", "sq_destroy", "sq_last_error",
 ]
 SQ_K_STENCIL = 0
 SQ_K_PROJECT = 1
@@ -113,6 +113,9 @@ def lib():
         L.sq_server_pending.restype = C.c_int
         L.sq_server_destroy.argtypes = [C.c_void_p]
         L.sq_server_destroy.restype = None
+        L.sq_green_kubo.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]
+        L.sq_green_kubo.restype = C.c_int
         L.sq_destroy.argtypes = [H]
         L.sq_destroy.restype = None
         L.sq_last_error.argtypes = [H]
@@ -297,6 +300,20 @@ def sq_batch_evaluate(handles, max_concurrent: int = 0):
         raise SQError(rc, "sq_batch_evaluate failed (see the handles' sq_last_error)")
     energies = [{k: getattr(en[i], k) for k, _ in sq_energies._fields_} for i in range(n)]
     return mu, energies, sig.reshape(n, 3, 3)
+
+
+def sq_green_kubo(sigma, dt: float, volume: float, kT: float, max_lag: int, stream=None):
+    """sigma: (n_traj, n_steps, 3, 3) stresses (Ha/bohr^3). Returns (eta (max_lag + 1,), acf)."""
+    sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+    if sig.ndim != 4 or sig.shape[2:] != (3, 3):
+        raise ValueError("sigma must have shape (n_traj, n_steps, 3, 3)")
+    eta = np.zeros(max_lag + 1)
+    acf = np.zeros(max_lag + 1)
+    rc = lib().sq_green_kubo(sig.ctypes.data, sig.shape[0], sig.shape[1], C.c_double(dt), C.c_double(volume),
+                             C.c_double(kT), int(max_lag), stream, eta.ctypes.data, acf.ctypes.data)
+    if rc != SQ_OK:
+        raise SQError(rc, sq_last_error(None))
+    return eta, acf
 
 
 class Server:

@@ -100,3 +100,16 @@ def test_server_rejects_invalid_descriptor(sq):
             srv.submit(d, tag=1)
     finally:
         srv.close()
+
+
+def test_green_kubo_rejects_bad_arguments_before_any_device_work(sq):
+    import numpy as np
+    sig = np.zeros((1, 10, 3, 3))
+    for kw in (dict(max_lag=10), dict(max_lag=-1), dict(dt=0.0), dict(volume=-1.0), dict(kT=0.0)):
+        args = dict(dt=1.0, volume=1.0, kT=1.0, max_lag=3)
+        args.update(kw)
+        with pytest.raises(sq.SQError) as ei:
+            sq.sq_green_kubo(sig, **args)
+        assert ei.value.code == sq.SQ_ERR_INVALID_ARG
+    with pytest.raises(sq.SQError):
+        sq.sq_green_kubo(np.zeros((1, 1, 3, 3)), 1.0, 1.0, 1.0, 0)

@@ -82,3 +82,39 @@ def test_server_mix_equals_alone(sq, alone):
         assert srv.pending() == 0
     finally:
         srv.close()
+
+
+def test_served_trajectory_green_kubo(sq):
+    """A synthetic trajectory (successively perturbed positions of one cell) served through the
+    request loop, its stress stream fed to sq_green_kubo: every request succeeds, results come
+    back for every step, the autocorrelation at lag 0 is the mean squared deviatoric stress of
+    the stream and the running viscosity starts at 0."""
+    from workloads import gaussian_veff, perturb_positions
+    base = tiny_instance(seed=31, n=(6, 6, 6), h=(0.7, 0.7, 0.7), n_atoms=3, n_o=2, r_cut=2.0, n_pl=16)
+    rng = np.random.Generator(np.random.PCG64(31))
+    steps = 8
+    srv = sq.Server(hbm_budget_bytes=4 << 30, max_inflight=4)
+    descs, pos = [], np.asarray(base["pos"])
+    try:
+        for k in range(steps):
+            pos = perturb_positions(rng, pos, 0.05, base["L"])
+            inst = dict(base)
+            inst["pos"] = pos
+            inst["v_eff"] = gaussian_veff(base["L"], base["n"], pos)
+            d = sq.Desc(inst, sq.SQ_FP64, bounds=(-1.0, 20.0))   # contains [0.64, 15.1] with margin
+            descs.append(d)
+            srv.submit(d, tag=k)
+        got = []
+        for _ in range(600):
+            got += srv.poll(timeout_ms=100)
+            if len(got) == steps:
+                break
+    finally:
+        srv.close()
+    assert len(got) == steps and all(r["status"] == sq.SQ_OK for r in got)
+    sig = np.array([r["sigma"] for r in sorted(got, key=lambda r: r["tag"])]).reshape(1, steps, 3, 3)
+    eta, acf = sq.sq_green_kubo(sig, 16.5, float(np.prod(base["L"])), float(base["kT"]), steps // 2)
+    s = np.stack([sig[0, :, 0, 1], sig[0, :, 1, 2], sig[0, :, 2, 0], 0.5 * (sig[0, :, 0, 0] - sig[0, :, 1, 1]),
+                  0.5 * (sig[0, :, 1, 1] - sig[0, :, 2, 2])], axis=1)
+    assert acf[0] == pytest.approx(float(np.mean(s * s)), rel=1e-12)
+    assert eta[0] == 0.0 and np.all(np.isfinite(eta))
