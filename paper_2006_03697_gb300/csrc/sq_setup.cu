@@ -106,19 +106,23 @@ __global__ void k_tile_entries(Geo g, Wave w, const AtomTab* __restrict__ atoms,
 
 // Support sphere of an atom image against a lattice box [bl, bhi] (absolute coords): the
 // table box overlaps it and the distance from the image centre to its bounding box is <= rcut.
-__device__ __forceinline__ bool image_meets_box(const Geo& g, const TileEntry& te, const AtomTab& at, double rc,
+// FP32 on small, box-relative coordinates (FP64 instructions issue at a small fraction of FP32
+// on this part) with a relative margin of 1e-5 on rcut^2, so the test never drops an image the
+// FP64 table holds non-zero values for (an extra image only adds zeros).
+__device__ __forceinline__ bool image_meets_box(const Geo& g, const TileEntry& te, const AtomTab& at, float rc,
                                                 const int bl[3], const int bhi[3]) {
   bool hit = true;
-  double d2 = 0.0;
+  float d2 = 0.f;
   for (int a = 0; a < 3; ++a) {
     const int lo = at.lo[a] + te.s[a] * g.n[a], hi = lo + at.dim[a] - 1;
     hit = hit && (lo <= bhi[a]) && (hi >= bl[a]);
-    const double c = at.R[a] + te.s[a] * g.L[a];
-    const double blo = bl[a] * g.h[a], bhi_x = bhi[a] * g.h[a];
-    const double dd = (c < blo) ? blo - c : (c > bhi_x ? c - bhi_x : 0.0);
+    // relative to the lattice point lo: image centre at -dlo, box from (bl - lo) h to (bhi - lo) h
+    const float h = float(g.h[a]), c = -at.dlo[a];
+    const float blo = float(bl[a] - lo) * h, bhx = float(bhi[a] - lo) * h;
+    const float dd = (c < blo) ? blo - c : (c > bhx ? c - bhx : 0.f);
     d2 += dd * dd;
   }
-  return hit && (d2 <= rc * rc * (1.0 + 1e-12) + 1e-24);
+  return hit && (d2 <= rc * rc * (1.f + 1e-5f) + 1e-10f);
 }
 
 // One warp per (brick, tile): entries whose support sphere meets the brick, in entry order,
@@ -156,8 +160,9 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
     if (e < ne) {
       te = ent[e];
       at = atoms[te.atom];
-      hit = image_meets_box(g, te, at, rcmax[te.atom], bl, bhi);
-      if (image_meets_box(g, te, at, rcmax[te.atom], sl, shi)) nch_slab = at.nch;
+      const float rcf = float(rcmax[te.atom]);
+      hit = image_meets_box(g, te, at, rcf, bl, bhi);
+      if (image_meets_box(g, te, at, rcf, sl, shi)) nch_slab = at.nch;
     }
     // slab-local first row of the lane's entry: exclusive warp scan of the slab entries' rows
     int incl = nch_slab;
@@ -185,20 +190,21 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
       const int srow_s = __shfl_sync(0xffffffffu, srow, src);
       int l0[3];
       for (int a = 0; a < 3; ++a) l0[a] = bl[a] - (ats.lo[a] + tes.s[a] * g.n[a]);
-      const double rc = rcmax[tes.atom];
+      const float rc = float(rcmax[tes.atom]);
       bool inpt[2];
       for (int hh = 0; hh < 2; ++hh) {
         const int pbit = lane + 32 * hh;
         const int pl[3] = {pbit & 3, (pbit >> 2) & 3, pbit >> 4};
         bool in = true;
-        double r2 = 0.0;
+        float r2 = 0.f;
         for (int a = 0; a < 3; ++a) {
           const int l = l0[a] + pl[a];
           in = in && (bl[a] + pl[a] <= bhi[a]) && l >= 0 && l < ats.dim[a];
-          const double d = (ats.lo[a] + l) * g.h[a] - ats.R[a];
+          const float d = float(l) * float(g.h[a]) + ats.dlo[a];   // (lo + l) h - R, box-relative
           r2 += d * d;
         }
-        inpt[hh] = in && r2 <= rc * rc;
+        // superset of the table's non-zero points (FP32 with a 1e-5 margin on rcut^2)
+        inpt[hh] = in && r2 <= rc * rc * (1.f + 1e-5f) + 1e-10f;
       }
       const unsigned lo32 = __ballot_sync(0xffffffffu, inpt[0]);
       const unsigned hi32 = __ballot_sync(0xffffffffu, inpt[1]);
