@@ -213,7 +213,9 @@ int build_wave_lists(sq_handle* h, const Wave& w);
 // sweep (sq_sweep.cu)
 int run_sweep(sq_handle* h);
 // out = H_q v for every node column of the wave's tiles (FP64), P = projection scratch
-int launch_apply_h64(sq_handle* h, const Wave& w, const double* v, double* out, double* P);
+// H_q v on the sample tiles of the Lanczos bounds (FP64 or FP32 vectors, matching tables)
+int launch_apply_h(sq_handle* h, const Wave& w, const double* v, double* out, double* P);
+int launch_apply_h(sq_handle* h, const Wave& w, const float* v, float* out, float* P);
 // entries / brick lists of a wave only (no A, W, t^0)
 int build_wave_entries(sq_handle* h, const Wave& w);
 

@@ -1,4 +1,6 @@
-// Spectral bounds for the Chebyshev scaling chi_q, zeta_q of Sec. 4 (FP64).
+// Spectral bounds for the Chebyshev scaling chi_q, zeta_q of Sec. 4 (FP64 for SQ_FP64; for
+// SQ_MIXED the Krylov vectors and H_q applications are FP32, the Gram-Schmidt coefficients,
+// tridiagonal and Ritz values FP64 - the bounds are widened by 1 % of the width anyway).
 //
 // The paper takes chi_q and zeta_q from the extreme eigenvalues of H_q and does not say how
 // they are obtained. Here: k-step Lanczos on the nodal Hamiltonian H_q of every node of a few
@@ -12,9 +14,13 @@
 
 namespace sq {
 
+constexpr int kTileLz = 8;              // nodes per tile (columns per tile)
+constexpr int kMaxLanczosVecs = 136;    // Krylov vectors held (k + 1, k <= 128 + 7)
+
 // Start vector of the column of node q: 1 + (hash(i, node) mod 1009) / 1009 on the window
 // (i = window-local index, C order z, y, x), zero elsewhere; normalised afterwards.
-__global__ void k_lz_init(Geo g, Wave w, double* __restrict__ V0) {
+template <typename Real>
+__global__ void k_lz_init(Geo g, Wave w, Real* __restrict__ V0) {
   const size_t per_tile = (size_t)g.Upts * g.B;
   const size_t total = per_tile * w.ntiles;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
@@ -34,22 +40,24 @@ __global__ void k_lz_init(Geo g, Wave w, double* __restrict__ V0) {
       const unsigned long long hsh = (i * 2654435761ull + node * 40503ull) & 0xFFFFFFFFull;
       v = 1.0 + double(hsh % 1009ull) / 1009.0;
     }
-    V0[idx] = v;
+    V0[idx] = Real(v);
   }
 }
 
-// out[col * ld + i] = <V_i, x>_col for i < nvec (one block per (i, tile); fixed-order sums)
-__global__ void k_lz_dots(Geo g, Wave w, const double* __restrict__ V, int nvec, size_t vstride,
-                          const double* __restrict__ x, double* __restrict__ out, int ld) {
+// out[col * ld + i] = <V_i, x>_col for i < nvec (one block per (i, tile); fixed-order sums:
+// per thread in the vectors' precision, across threads in FP64)
+template <typename Real>
+__global__ void k_lz_dots(Geo g, Wave w, const Real* __restrict__ V, int nvec, size_t vstride,
+                          const Real* __restrict__ x, double* __restrict__ out, int ld) {
   const int i = blockIdx.x, tl = blockIdx.y;
   const size_t base = (size_t)tl * g.Upts * g.B;
-  const double* Vi = V + (size_t)i * vstride + base;
-  const double* xt = x + base;
+  const Real* Vi = V + (size_t)i * vstride + base;
+  const Real* xt = x + base;
   const int q = threadIdx.x % g.B;
-  double s = 0.0;
+  Real s = Real(0);
   for (int e = threadIdx.x; e < g.Upts * g.B; e += blockDim.x) s += Vi[e] * xt[e];
   __shared__ double red[kThreads];
-  red[threadIdx.x] = s;
+  red[threadIdx.x] = double(s);
   __syncthreads();
   if (threadIdx.x < g.B) {
     double t = 0.0;
@@ -58,18 +66,25 @@ __global__ void k_lz_dots(Geo g, Wave w, const double* __restrict__ V, int nvec,
   }
 }
 
-// x -= sum_i coef[col * ld + i] V_i
-__global__ void k_lz_update(Geo g, Wave w, const double* __restrict__ V, int nvec, size_t vstride,
-                            const double* __restrict__ coef, int ld, double* __restrict__ x) {
+// x -= sum_i coef[col * ld + i] V_i; grid (blocks per tile, tiles): a block's coefficients
+// (8 columns x nvec) are converted to the vectors' precision once, in shared memory
+template <typename Real>
+__global__ void k_lz_update(Geo g, Wave w, const Real* __restrict__ V, int nvec, size_t vstride,
+                            const double* __restrict__ coef, int ld, Real* __restrict__ x) {
+  __shared__ Real cf[kTileLz][kMaxLanczosVecs];
+  const int tl = blockIdx.y;
+  for (int k2 = threadIdx.x; k2 < g.B * nvec; k2 += blockDim.x) {
+    const int q = k2 / nvec, i = k2 % nvec;
+    cf[q][i] = Real(coef[((size_t)tl * g.B + q) * ld + i]);
+  }
+  __syncthreads();
   const size_t per_tile = (size_t)g.Upts * g.B;
-  const size_t total = per_tile * w.ntiles;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int tl = int(idx / per_tile);
-    const int q = int(idx % per_tile) % g.B;
-    const double* c = coef + ((size_t)tl * g.B + q) * ld;
-    double acc = 0.0;
-    for (int i = 0; i < nvec; ++i) acc += c[i] * V[(size_t)i * vstride + idx];
-    x[idx] -= acc;
+  const size_t base = per_tile * tl;
+  for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < per_tile; r += (size_t)gridDim.x * blockDim.x) {
+    const int q = int(r % g.B);
+    Real acc = Real(0);
+    for (int i = 0; i < nvec; ++i) acc += cf[q][i] * V[(size_t)i * vstride + base + r];
+    x[base + r] -= acc;
   }
 }
 
@@ -89,8 +104,9 @@ __global__ void k_lz_step(int ncols, int i, int kk, int k, const double* __restr
 
 // V_next = x / beta for running columns (zero otherwise). With first != 0: normalise the
 // start vector in place (beta = sqrt(nrm)); a zero start vector marks an empty column.
-__global__ void k_lz_scale(Geo g, Wave w, const double* __restrict__ x, const double* __restrict__ nrm, int ld,
-                           int* __restrict__ keff, double* __restrict__ Vn, int first) {
+template <typename Real>
+__global__ void k_lz_scale(Geo g, Wave w, const Real* __restrict__ x, const double* __restrict__ nrm, int ld,
+                           int* __restrict__ keff, Real* __restrict__ Vn, int first) {
   const size_t per_tile = (size_t)g.Upts * g.B;
   const size_t total = per_tile * w.ntiles;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
@@ -99,7 +115,7 @@ __global__ void k_lz_scale(Geo g, Wave w, const double* __restrict__ x, const do
     const size_t col = (size_t)tl * g.B + q;
     const double b = sqrt(nrm[col * ld]);
     const bool run = first ? (b > 0.0) : (keff[col] < 0);
-    Vn[idx] = run ? x[idx] / b : 0.0;
+    Vn[idx] = run ? Real(double(x[idx]) / b) : Real(0);
   }
 }
 
@@ -196,7 +212,8 @@ __global__ void k_lz_bounds(int ncols, int k, const double* __restrict__ alpha, 
   }
 }
 
-int run_lanczos(sq_handle* h) {
+template <typename Real>
+static int run_lanczos_t(sq_handle* h) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
   const int nst = int(h->lanczos_tiles.size());
@@ -208,8 +225,8 @@ int run_lanczos(sq_handle* h) {
   const int ld = k + 1;
   const Wave w{0, nst, h->d.lz_tiles};
   const size_t vstride = (size_t)nst * g.Upts * g.B;
-  double* V = h->d.lzV;
-  double* W = h->d.lzW;
+  Real* V = reinterpret_cast<Real*>(h->d.lzV);   // buffers sized for FP64
+  Real* W = reinterpret_cast<Real*>(h->d.lzW);
   double* cA = h->d.lzC;
   double* cB = cA + (size_t)ncols * ld;
   double* nrm = cB + (size_t)ncols * ld;
@@ -217,35 +234,36 @@ int run_lanczos(sq_handle* h) {
   double* beta = alpha + (size_t)ncols * k;
   int* keff = (int*)(beta + (size_t)ncols * k);
   const int eb = 1024;
+  const int ub = int(std::min<size_t>(64, ((size_t)g.Upts * g.B + 255) / 256));   // update blocks per tile
   const int cb = (ncols + 127) / 128;
   int rc = build_wave_entries(h, w);
   if (rc != SQ_OK) return rc;
-  k_lz_init<<<eb, 256, 0, s>>>(g, w, V);
+  k_lz_init<Real><<<eb, 256, 0, s>>>(g, w, V);
   SQ_LAUNCH_CHECK(h);
-  k_lz_dots<<<dim3(1, nst), kThreads, 0, s>>>(g, w, V, 1, vstride, V, nrm, ld);
+  k_lz_dots<Real><<<dim3(1, nst), kThreads, 0, s>>>(g, w, V, 1, vstride, V, nrm, ld);
   SQ_LAUNCH_CHECK(h);
   k_lz_mark_empty<<<cb, 128, 0, s>>>(ncols, nrm, ld, keff);
   SQ_LAUNCH_CHECK(h);
-  k_lz_scale<<<eb, 256, 0, s>>>(g, w, V, nrm, ld, keff, V, 1);
+  k_lz_scale<Real><<<eb, 256, 0, s>>>(g, w, V, nrm, ld, keff, V, 1);
   SQ_LAUNCH_CHECK(h);
   for (int i = 0; i < kk; ++i) {
-    double* Vi = V + (size_t)i * vstride;
-    rc = launch_apply_h64(h, w, Vi, W, h->d.lzP);
+    Real* Vi = V + (size_t)i * vstride;
+    rc = launch_apply_h(h, w, Vi, W, reinterpret_cast<Real*>(h->d.lzP));
     if (rc != SQ_OK) return rc;
-    k_lz_dots<<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cA, ld);
+    k_lz_dots<Real><<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cA, ld);
     SQ_LAUNCH_CHECK(h);
-    k_lz_update<<<eb, 256, 0, s>>>(g, w, V, i + 1, vstride, cA, ld, W);
+    k_lz_update<Real><<<dim3(ub, nst), 256, 0, s>>>(g, w, V, i + 1, vstride, cA, ld, W);
     SQ_LAUNCH_CHECK(h);
-    k_lz_dots<<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cB, ld);
+    k_lz_dots<Real><<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cB, ld);
     SQ_LAUNCH_CHECK(h);
-    k_lz_update<<<eb, 256, 0, s>>>(g, w, V, i + 1, vstride, cB, ld, W);
+    k_lz_update<Real><<<dim3(ub, nst), 256, 0, s>>>(g, w, V, i + 1, vstride, cB, ld, W);
     SQ_LAUNCH_CHECK(h);
-    k_lz_dots<<<dim3(1, nst), kThreads, 0, s>>>(g, w, W, 1, vstride, W, nrm, ld);
+    k_lz_dots<Real><<<dim3(1, nst), kThreads, 0, s>>>(g, w, W, 1, vstride, W, nrm, ld);
     SQ_LAUNCH_CHECK(h);
     k_lz_step<<<cb, 128, 0, s>>>(ncols, i, kk, k, cA, cB, ld, nrm, alpha, beta, keff);
     SQ_LAUNCH_CHECK(h);
     if (i < kk - 1) {
-      k_lz_scale<<<eb, 256, 0, s>>>(g, w, W, nrm, ld, keff, V + (size_t)(i + 1) * vstride, 0);
+      k_lz_scale<Real><<<eb, 256, 0, s>>>(g, w, W, nrm, ld, keff, V + (size_t)(i + 1) * vstride, 0);
       SQ_LAUNCH_CHECK(h);
     }
   }
@@ -257,6 +275,12 @@ int run_lanczos(sq_handle* h) {
   if (!(b2[0] < b2[1]) || !std::isfinite(b2[0]) || !std::isfinite(b2[1]))
     return fail(h, SQ_ERR_CUDA, "Lanczos bounds are not finite");
   return set_bounds(h, b2[0], b2[1]);
+}
+
+int run_lanczos(sq_handle* h) {
+  if (h->lanczos_k + 1 > kMaxLanczosVecs) return fail(h, SQ_ERR_INVALID_ARG, "lanczos_k too large");
+  if (h->precision == SQ_MIXED) return run_lanczos_t<float>(h);
+  return run_lanczos_t<double>(h);
 }
 
 }  // namespace sq

@@ -797,16 +797,25 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
   return SQ_OK;
 }
 
-int launch_apply_h64(sq_handle* h, const Wave& w, const double* v, double* out, double* P) {
+template <typename Real>
+static int apply_h_t(sq_handle* h, const Wave& w, const Real* v, Real* out, Real* P, const Real* chi, const Real* vpot) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  k_project<double><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, h->d.chi64, h->d.atoms, h->d.gdv,
-                                                                  h->wb.entries, h->wb.n_entries, P);
+  k_project<Real><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, chi, h->d.atoms, h->d.gdv, h->wb.entries,
+                                                               h->wb.n_entries, P);
   SQ_LAUNCH_CHECK(h);
-  k_apply_h<double><<<dim3(g.nslab, w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, h->d.chi64, h->d.atoms, h->wb.entries,
-                                                                  h->wb.brick_list, h->wb.brick_n, h->d.v64);
+  k_apply_h<Real><<<dim3(g.nslab, w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, chi, h->d.atoms, h->wb.entries,
+                                                               h->wb.brick_list, h->wb.brick_n, vpot);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
+}
+
+int launch_apply_h(sq_handle* h, const Wave& w, const double* v, double* out, double* P) {
+  return apply_h_t<double>(h, w, v, out, P, h->d.chi64, h->d.v64);
+}
+
+int launch_apply_h(sq_handle* h, const Wave& w, const float* v, float* out, float* P) {
+  return apply_h_t<float>(h, w, v, out, P, h->d.chi32, h->d.v32);
 }
 
 int run_sweep(sq_handle* h) {

@@ -230,6 +230,23 @@ def test_lanczos_bounds_parity(sq, name):
     assert abs(ghi - hi) <= 1e-9 * (hi - lo)
 
 
+@pytest.mark.parametrize("name", ["ragged_sp", "no_atoms", "m1_no1", "thin_cell"])
+def test_lanczos_bounds_mixed(sq, name):
+    """Mixed precision runs the Lanczos vectors and H_q applications in FP32 (FP64 Gram-Schmidt
+    coefficients and tridiagonal): its interval (after the FP32-exact scaling) is the oracle's
+    to 1e-5 of the width, far inside the 1 % widening."""
+    inst = tiny_instance(**TINY[name])
+    lo, hi = orc.lanczos_bounds(orc.Problem(inst))
+    h = sq.sq_setup(sq.Desc(inst, sq.SQ_MIXED))
+    try:
+        sq.sq_moments(h)
+        glo, ghi = sq.sq_get_bounds(h)
+    finally:
+        sq.sq_destroy(h)
+    assert abs(glo - lo) <= 1e-5 * (hi - lo)
+    assert abs(ghi - hi) <= 1e-5 * (hi - lo)
+
+
 def test_full_default_path_config1(sq, config1_ref):
     """Default path (device Lanczos bounds) against the oracle with its own Lanczos bounds."""
     inst, bounds, o = config1_ref
