@@ -259,73 +259,105 @@ __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
 
 // W_b(u, q) = sum_rows gamma |dOmega| A[row][q] chi_row(u) (x_u,b - R_b) on the window of q:
 // contracting the atom sum of the sigma^III term once, S^j_ab = sum_u W_b(u,q) (grad_a t^j)(u).
+// One block per (z-slab, tile); each warp walks whole 4^3 bricks (lanes = 4 x-points x 8
+// nodes) and, per half brick (8 points per lane, accumulators in registers), the brick's image
+// records: the 64-bit sphere mask skips the points an image does not reach, the table offset
+// of the brick corner locates the point's channel group.
 template <typename Real>
-__global__ void k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const Real* __restrict__ gdv,
-                         const Real* __restrict__ chi,
-                         const TileEntry* __restrict__ entries, const int* __restrict__ blist,
-                         const int* __restrict__ bn, const Real* __restrict__ A, Real* __restrict__ W) {
+__global__ void __launch_bounds__(256) k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms,
+                                                const Real* __restrict__ gdv, const Real* __restrict__ chi,
+                                                const TileEntry* __restrict__ entries, const int* __restrict__ blist,
+                                                const int4* __restrict__ brec, const int* __restrict__ bn,
+                                                const Real* __restrict__ A, Real* __restrict__ W) {
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int o[3];
   tile_origin(g, t, o);
-  const int z0 = slab * kBrick, nz = min(kBrick, g.U[2] - z0);
-  const int nel = g.U[0] * g.U[1] * nz * g.B;
   const TileEntry* ent = entries + (size_t)tl * g.e_cap;
   const Real* At = A + (size_t)tl * g.r_cap * g.B;
   Real* Wt = W + (size_t)tl * 3 * g.Upts * g.B;
+  const size_t wstr = (size_t)g.Upts * g.B;
+  const int q = lane & 7, pa = lane >> 3;
+  int qo[3];
+  node_offset(g, q, qo);
+  const bool valid = node_valid(g, o, qo);
   const Real hr[3] = {Real(g.h[0]), Real(g.h[1]), Real(g.h[2])};
-  for (int i = threadIdx.x; i < nel; i += blockDim.x) {
-    const int q = i % g.B, p = i / g.B;
-    const int ux = p % g.U[0], uy = (p / g.U[0]) % g.U[1], uz = z0 + p / (g.U[0] * g.U[1]);
-    const int pt = (uz * g.U[1] + uy) * g.U[0] + ux;
-    int qo[3];
-    node_offset(g, q, qo);
-    Real acc[3] = {Real(0), Real(0), Real(0)};
-    if (node_valid(g, o, qo) && in_window(g, qo, ux, uy, uz)) {
-      const int ax[3] = {o[0] - g.m[0] + ux, o[1] - g.m[1] + uy, o[2] - g.m[2] + uz};
-      const int br = ((uz / kBrick) * g.nbr[1] + uy / kBrick) * g.nbr[0] + ux / kBrick;
-      const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
-      const int nb = bn[(size_t)tl * g.nbricks + br];
+  const int nbx = g.nbr[0], nby = g.nbr[1];
+  for (int bi = warp; bi < nbx * nby; bi += nw) {
+    const int bx = bi % nbx, by = bi / nbx;
+    const int br = (slab * nby + by) * nbx + bx;
+    const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
+    const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
+    const int nb = bn[(size_t)tl * g.nbricks + br];
+    const int bl[3] = {o[0] - g.m[0] + bx * kBrick, o[1] - g.m[1] + by * kBrick, o[2] - g.m[2] + slab * kBrick};
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      Real acc[8][3];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = Real(0);
       for (int k = 0; k < nb; ++k) {
+        const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
+        const unsigned mk = unsigned(half ? r1.w : r1.z) >> pa;   // bits pa + 4 i of this half
+        if (!(mk & 0x11111111u)) continue;
         const TileEntry te = ent[lst[k]];
         const AtomTab& at = atoms[te.atom];
-        int l[3];
-        bool in = true;
-        for (int b = 0; b < 3; ++b) {
-          l[b] = ax[b] - te.s[b] * g.n[b] - at.lo[b];
-          in = in && (unsigned)l[b] < (unsigned)at.dim[b];
-        }
-        if (!in) continue;
-        const Real* cr = chi_row(chi, at, (l[2] * at.dim[1] + l[1]) * at.dim[0] + l[0]);
-        Real cs = Real(0);   // accumulated in the sweep's precision (FP32 suffices for the mixed path)
-        for (int c = 0; c < at.nch; ++c) cs += gdv[at.ch0 + c] * At[(size_t)(te.row0 + c) * g.B + q] * cr[c];
-        if (cs == Real(0)) continue;
-        // x_b - R_b of the image: l_b h_b + (lo_b h_b - R_b) (the image shift s n h = s L cancels)
-        for (int b = 0; b < 3; ++b) {
-          const Real d = (sizeof(Real) == 4) ? Real(l[b]) * hr[b] + Real(at.dlo[b])
-                                             : Real((at.lo[b] + l[b]) * g.h[b] - at.R[b]);
-          acc[b] += cs * d;
+        int l0[3];   // box-local lattice coordinates of the brick corner
+#pragma unroll
+        for (int b = 0; b < 3; ++b) l0[b] = bl[b] - (at.lo[b] + te.s[b] * g.n[b]);
+        const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
+        for (int c0 = 0; c0 < nch; c0 += 4) {
+          Real ag[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            ag[c] = (c0 + c < nch) ? gdv[r0.z + c0 + c] * At[(size_t)(r0.y + c0 + c) * g.B + q] : Real(0);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if ((mk >> (4 * i)) & 1u) {
+              const int it = 8 * half + i, pb = it & 3, pc = it >> 2;
+              const Real* cr = chi + r0.x + ((pc * r1.y + pb) * r1.x + pa) * nchp + c0;
+              Real cs = Real(0);   // accumulated in the sweep's precision (FP32 suffices for the mixed path)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) cs += ag[c] * cr[c];
+              if (cs == Real(0)) continue;
+              const int l[3] = {l0[0] + pa, l0[1] + pb, l0[2] + pc};
+              // x_b - R_b of the image: l_b h_b + (lo_b h_b - R_b) (the image shift s n h = s L cancels)
+#pragma unroll
+              for (int b = 0; b < 3; ++b) {
+                const Real d = (sizeof(Real) == 4) ? Real(l[b]) * hr[b] + Real(at.dlo[b])
+                                                   : Real((at.lo[b] + l[b]) * g.h[b] - at.R[b]);
+                acc[i][b] += cs * d;
+              }
+            }
+          }
         }
       }
+      // the half brick's 8 points of this lane: write W (zero outside the node's window)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int it = 8 * half + i;
+        const int ux = bx * kBrick + pa, uy = by * kBrick + (it & 3), uz = slab * kBrick + (it >> 2);
+        if (uy >= g.U[1] || uz >= g.U[2]) continue;
+        const bool inw = valid && in_window(g, qo, ux, uy, uz);
+        const size_t e = ((size_t)(uz * g.U[1] + uy) * g.U[0] + ux) * g.B + q;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Wt[b * wstr + e] = inw ? acc[i][b] : Real(0);
+      }
     }
-    for (int b = 0; b < 3; ++b) Wt[((size_t)b * g.Upts + pt) * g.B + q] = acc[b];
   }
 }
 
 // t^0 = w_q: one at the node's own point, zero elsewhere (and zero columns for padding nodes).
 template <typename Real>
 __global__ void k_init_t0(Geo g, Wave w, Real* __restrict__ T0) {
-  const size_t per_tile = (size_t)g.Upts * g.B;
-  const size_t total = per_tile * w.ntiles;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int tl = int(i / per_tile);
-    const int r = int(i % per_tile);
-    const int q = r % g.B, pt = r / g.B;
-    int o[3], qo[3];
-    tile_origin(g, wave_tile(w, tl), o);
-    node_offset(g, q, qo);
-    const int cpt = ((qo[2] + g.m[2]) * g.U[1] + (qo[1] + g.m[1])) * g.U[0] + (qo[0] + g.m[0]);
-    T0[i] = (node_valid(g, o, qo) && pt == cpt) ? Real(1) : Real(0);
-  }
+  // T0 was cleared; set t^0 = e_q: 1 at each valid node's own point of the union window
+  const int tl = blockIdx.x * blockDim.y + threadIdx.y, q = threadIdx.x;
+  if (tl >= w.ntiles) return;
+  int o[3], qo[3];
+  tile_origin(g, wave_tile(w, tl), o);
+  node_offset(g, q, qo);
+  if (!node_valid(g, o, qo)) return;
+  const int cpt = ((qo[2] + g.m[2]) * g.U[1] + (qo[1] + g.m[1])) * g.U[0] + (qo[0] + g.m[0]);
+  T0[((size_t)tl * g.Upts + cpt) * g.B + q] = Real(1);
 }
 
 template <typename Real>
@@ -342,10 +374,11 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, const Real
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
                                           (double*)h->wb.Pg[0], (double*)h->wb.Pg[1]);
   SQ_LAUNCH_CHECK(h);
-  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 256, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries, h->wb.brick_list,
-                                                          h->wb.brick_n, A, W);
+  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 224, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries, h->wb.brick_list,
+                                                          h->wb.brick_rec, h->wb.brick_n, A, W);
   SQ_LAUNCH_CHECK(h);
-  k_init_t0<Real><<<1024, 256, 0, s>>>(g, w, T0);
+  SQ_CUDA_TRY(h, cudaMemsetAsync(T0, 0, sizeof(Real) * (size_t)w.ntiles * g.Upts * g.B, s));
+  k_init_t0<Real><<<(w.ntiles + 31) / 32, dim3(g.B, 32), 0, s>>>(g, w, T0);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }
