@@ -132,6 +132,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def step_kernel_hash() -> str:
+    """sha1 of the step kernel's source text (its device helpers and the kernel, through its
+    end, plus sq_device.cuh): the committed traffic figure is valid for that text only."""
+    csrc = os.path.join(ROOT, "paper_2006_03697_gb300", "csrc")
+    src = open(os.path.join(csrc, "sq_sweep.cu")).read()
+    start = src.index("template <typename Real> struct Coef;")
+    end = src.index("__constant__ int c_kpairs", start)
+    dev = open(os.path.join(csrc, "sq_device.cuh")).read()
+    return hashlib.sha1((src[start:end] + dev).encode()).hexdigest()
+
+
 def stencil_traffic(sweep_hash: str):
     """Per-launch DRAM traffic of the stencil kernel from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
@@ -139,7 +150,7 @@ def stencil_traffic(sweep_hash: str):
     try:
         with open(path) as f:
             t = json.load(f)
-        if t.get("sweep_source_sha1") == sweep_hash:
+        if t.get("step_kernel_sha1") == sweep_hash:
             return float(t["bytes_per_launch_full_size"])
     except (OSError, KeyError, ValueError):
         pass
@@ -358,8 +369,7 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     dom = max(kern, key=lambda k: kern[k]["ms"])
     st = kern["stencil"]
-    sweep_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2006_03697_gb300", "csrc", "sq_sweep.cu"),
-                                   "rb").read()).hexdigest()
+    sweep_hash = step_kernel_hash()
     achieved = (st["bytes"] / st["launches"]) / (st["ms"] / st["launches"] / 1000.0) / 1e9 if st["launches"] else 0.0
     roof = {"kernel": "k_stencil", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": stencil_traffic(sweep_hash),

@@ -4,20 +4,23 @@
 // and the per-node moments rho^j, K^j_ab, N^j, S^j_ab of each column.
 //
 // Kernels (Real = double for SQ_FP64, float for SQ_MIXED; node sums always FP64):
-//   k_step      one block per (z-slab of 4 planes, tile); each warp walks whole 4^3 bricks,
-//               lanes = 4 x-points x the 8 nodes of the tile, 16 iterations per brick. Per
-//               element: Laplacian + V + nonlocal apply (Pg^j staged in shared memory, only
-//               the atom images whose support sphere holds the point, from a 64-bit mask),
-//               the window mask and the recurrence update, and the nonlocal-stress partial
-//               sum_u W_b (grad_a t^j) (the gradient taps reuse the Laplacian loads). Then,
-//               fused, the projections gamma |dOmega| chi^T t^{j+1} of the new column: summed
-//               over the brick in registers, a 3-shuffle reduce-scatter over the x-point lanes,
-//               one shared-memory add per (image, channel, node) issued by all 32 lanes at
-//               once, one global add per row and node per slab.
+//   k_step      one block per (z-slab of 4 planes, tile), 4..8 warps; each warp walks whole
+//               4^3 bricks, so the atom-image records of a brick (table offset, 64-bit mask of
+//               the points inside the support sphere) are warp-uniform. Per brick:
+//               A  the nonlocal apply sum_rows chi_row(u) Pg^j (Pg^j staged in shared memory);
+//                  SQ_MIXED: a TF32 tensor-core product over the brick (3-term hi/lo split,
+//                  tables stored pre-split), SQ_FP64: scalar and record-major;
+//               B  Laplacian + V + the apply, the window mask, the recurrence update and the
+//                  nonlocal-stress partial sum_u W_b (grad_a t^j) (the gradient taps reuse the
+//                  Laplacian loads); SQ_MIXED: two nodes per lane (8-byte loads);
+//               C  fused, the projections gamma |dOmega| chi^T t^{j+1} of the new column
+//                  (SQ_MIXED: the transposed tensor-core product; SQ_FP64: register sums and a
+//                  reduce-scatter over the point lanes), one shared-memory FP64 add per
+//                  (image, channel, node), one global add per row and node per slab.
 //   k_moments   one block per tile: rho^j, K^j (restricted grad_a grad_b at the node),
 //               N^j = sum_rows chi(x_q) Pg^j, S^j = sum of the slab partials; FP64 table
 //               row; then clears Pg^j, which accumulates the projections of step j + 1.
-//   k_apply_h / k_project   plain H_q v for the Lanczos bounds (FP64).
+//   k_apply_h / k_project   plain H_q v for the Lanczos bounds (sweep precision).
 #include <algorithm>
 
 #include "sq_device.cuh"

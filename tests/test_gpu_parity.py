@@ -72,6 +72,23 @@ def test_fp64_parity_tiny(sq, name):
     assert g["launches"] > 0
 
 
+@pytest.mark.parametrize("name", sorted(TINY))
+def test_mixed_parity_tiny(sq, name):
+    """The mixed path (tensor-core projector phases where every atom has at most 4 channels,
+    paired stencil phase, FP32 Lanczos not used: bounds given) on the edge cases: energies
+    within 1e-6 relative of the oracle, sigma and the App. A pressure within 1e-5 Ha/bohr^3."""
+    inst = tiny_instance(**TINY[name])
+    bounds = orc.lanczos_bounds(orc.Problem(inst))
+    o = orc.run(inst, bounds=bounds)
+    g = sq.run(inst, sq.SQ_MIXED, bounds=bounds)
+    for key in ("E_band", "E_s", "F"):
+        assert abs(g[key] - o[key]) <= E_RTOL_MIXED * max(1.0, abs(o[key])), key
+    assert abs(g["E_nl"] - o["E_nl"]) <= E_RTOL_MIXED * max(1.0, abs(o["E_band"]))
+    assert np.abs(g["sigma"] - o["sigma"]).max() <= SIG_ATOL_MIXED
+    assert abs(g["pressure_A"] - o["pressure_A"]) <= SIG_ATOL_MIXED
+    assert abs(g["N_check"] - inst["n_e"]) <= 1e-9 * inst["n_e"]
+
+
 @pytest.fixture(scope="module")
 def config1_ref():
     inst = make_instance(1)
