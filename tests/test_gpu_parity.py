@@ -57,6 +57,12 @@ TINY = {
     "no6_truncated": dict(seed=4, n=(4, 4, 4), h=(0.5, 0.5, 0.5), n_atoms=2, n_o=6, r_cut=2.5, n_pl=12),
     # single node per cell along x, window wraps the cell many times
     "thin_cell": dict(seed=5, n=(1, 3, 2), h=(0.9, 0.8, 0.7), n_atoms=1, n_o=2, r_cut=2.0, n_pl=8),
+    # 5 channels per atom (two s, one p): channel groups beyond 4 (the scalar projector phases
+    # in both precisions)
+    "five_channels": dict(seed=6, n=(5, 5, 4), h=(0.7, 0.7, 0.7), n_atoms=2, n_o=3, r_cut=2.1, n_pl=14,
+                          proj=[{"l": 0, "width": 0.5, "gamma": 1.0, "rcut": 3.5},
+                                {"l": 0, "width": 0.8, "gamma": -0.3, "rcut": 3.5},
+                                {"l": 1, "width": 0.5, "gamma": 0.5, "rcut": 3.5}]),
 }
 
 
