@@ -14,4 +14,5 @@ Modules
   free_electron closed forms for V_eff = 0 and no projectors (Brillouin-zone integrals
                 and the exactly separable truncated region)
   green_kubo    Green-Kubo shear viscosity of a stress time series (Eq. viscosity)
+  per_node      the per-node spectral bounds mode (chi_q, zeta_q of each H_q)
 """

@@ -11,7 +11,7 @@ import pytest
 import scipy.integrate
 import scipy.linalg
 
-from oracle import dense_k, free_electron, green_kubo
+from oracle import dense_k, free_electron, green_kubo, per_node
 from oracle.sq_oracle import (K_PAIRS, NodeRegion, Problem, cheb_coeffs, chebyshev_columns, contract,
                               entropy_fn, fd_coefficients, fd_weights, fermi, fermi_bisect, lanczos_bounds,
                               node_moments, primed, run)
@@ -462,3 +462,43 @@ def test_p11_green_kubo_exponential_correlation():
     np.testing.assert_allclose(c[:4], np.exp(-np.arange(4) / tau) / 5.0, atol=0.01)
     expect = vol / kT * dt / 5.0 * 0.5 * (1.0 + a) / (1.0 - a)
     assert abs(eta[-1] - expect) < 0.1 * expect
+
+
+# ---------------------------------------------------------------- P12: per-node spectral bounds
+@pytest.fixture(scope="module")
+def per_node_case():
+    inst = tiny_instance(seed=11, n=(4, 4, 4), h=(0.8, 0.8, 0.8), n_atoms=3, n_o=3, r_cut=2.4, n_pl=24)
+    return inst, per_node.run(inst)
+
+
+def test_p12_per_node_intervals_contain_each_spectrum(per_node_case):
+    """Each node's interval (Lanczos extremes with residual widening, then 1 %) contains the
+    whole spectrum of its H_q, from a dense symmetric eigensolver of the Kronecker-assembled
+    matrix; and it is no wider than needed by more than the 1 % margins plus the residuals."""
+    inst, out = per_node_case
+    prob = Problem(inst)
+    for q in (0, 21, 42, 63):
+        ev = np.linalg.eigvalsh(NodeRegion(prob, prob.node_coords(q)).dense_H())
+        lo, hi = out["bounds"][q]
+        assert lo <= ev[0] and ev[-1] <= hi
+        assert (hi - lo) <= 1.05 * (ev[-1] - ev[0])
+
+
+def test_p12_per_node_mode_reduces_to_shared_mode(per_node_case):
+    """Per-node code with every node given the shared interval reproduces the shared mode
+    exactly (moments, Fermi level, contraction); with its own intervals it converges to the
+    same density matrix (n_pl = 24 here: free energy and stress agree to 1e-12)."""
+    inst, out = per_node_case
+    prob = Problem(inst)
+    gb = lanczos_bounds(prob)
+    ref = run(inst, bounds=gb)
+    B = np.tile(np.array(gb), (prob.Nd, 1))
+    mom = per_node.moments(prob, B)
+    mu = per_node.fermi_bisect(prob, mom, B)
+    same = per_node.contract(prob, mom, B, mu)
+    assert mu == ref["mu"]
+    assert abs(same["F"] - ref["F"]) <= 1e-14 * abs(ref["F"])
+    np.testing.assert_allclose(same["sigma"], ref["sigma"], rtol=0, atol=1e-15)
+    assert abs(out["F"] - ref["F"]) <= 1e-12 * abs(ref["F"])
+    np.testing.assert_allclose(out["sigma"], ref["sigma"], rtol=0, atol=1e-12)
+    assert abs(out["N_check"] - inst["n_e"]) < 1e-10 * inst["n_e"]
