@@ -224,7 +224,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   size_t tileB = size_t(g.B);
   P.per_tile_bytes = size_t(g.e_cap) * sizeof(sq::TileEntry) + 2 * sizeof(int) +
                      size_t(g.nbricks) * (size_t(g.br_cap) + 1) * sizeof(int) +
-                     size_t(g.nbricks) * size_t(g.br_cap) * 2 * sizeof(int4) +
+                     size_t(g.nbricks) * size_t(g.br_cap) * 3 * sizeof(int4) +   // records + corner offsets
                      3 * size_t(g.Upts) * tileB * real +        // T ring
                      3 * size_t(g.Upts) * tileB * real +        // W
                      2 * size_t(g.r_cap) * tileB * real +       // A, P
@@ -459,6 +459,7 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->wb.brick_list, sizeof(int) * size_t(wt) * g.nbricks * g.br_cap);
   SQ_ALLOC(h->wb.brick_n, sizeof(int) * size_t(wt) * g.nbricks);
   SQ_ALLOC(h->wb.brick_rec, sizeof(int4) * 2 * size_t(wt) * g.nbricks * g.br_cap);
+  SQ_ALLOC(h->wb.brick_d0, sizeof(float4) * size_t(wt) * g.nbricks * g.br_cap);
   SQ_ALLOC(h->wb.slab_n, sizeof(int) * size_t(wt) * g.nslab);
   SQ_ALLOC(h->wb.slab_map, sizeof(int) * size_t(wt) * g.nslab * g.r_cap);
   for (int i = 0; i < 3; ++i) SQ_ALLOC(h->wb.T[i], real * size_t(wt) * g.Upts * g.B);

@@ -102,6 +102,7 @@ struct WaveBufs {
   int* brick_list = nullptr;      // [wt][nbricks][br_cap]
   int* brick_n = nullptr;         // [wt][nbricks]
   int4* brick_rec = nullptr;      // [wt][nbricks][br_cap][2] per-brick image records
+  float4* brick_d0 = nullptr;     // [wt][nbricks][br_cap] x - R of the record's brick corner (FP32 W table)
   int* slab_n = nullptr;          // [wt][nslab] projector rows meeting each z-slab
   int* slab_map = nullptr;        // [wt][nslab][r_cap] slab row -> tile row
   void* T[3] = {nullptr, nullptr, nullptr};   // Real [wt][Upts][B]

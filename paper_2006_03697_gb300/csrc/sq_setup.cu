@@ -133,7 +133,8 @@ __device__ __forceinline__ bool image_meets_box(const Geo& g, const TileEntry& t
 __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ rcmax,
                               const TileEntry* __restrict__ entries, const int* __restrict__ n_entries,
                               int* __restrict__ blist, int* __restrict__ bn, int4* __restrict__ rec,
-                              int* __restrict__ slab_n, int* __restrict__ slab_map, int* __restrict__ status) {
+                              float4* __restrict__ d0, int* __restrict__ slab_n, int* __restrict__ slab_map,
+                              int* __restrict__ status) {
   const int br = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl), lane = threadIdx.x;
   int o[3];
   tile_origin(g, t, o);
@@ -213,6 +214,11 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
         int4* r = rec + (((size_t)tl * g.nbricks + br) * g.br_cap + pos_s) * 2;
         r[0] = make_int4(offc, tes.row0, ats.ch0, ats.nch | (ats.nchp << 8) | (min(srow_s, 0xffff) << 16));
         r[1] = make_int4(ats.dim[0], ats.dim[1], int(lo32), int(hi32));
+        // x - R of the brick corner for this image, (lo + l0) h - R, formed in FP64 and rounded once
+        // (once per record: the per-point work adds only the in-brick offset)
+        d0[((size_t)tl * g.nbricks + br) * g.br_cap + pos_s] =
+            make_float4(float((ats.lo[0] + l0[0]) * g.h[0] - ats.R[0]), float((ats.lo[1] + l0[1]) * g.h[1] - ats.R[1]),
+                        float((ats.lo[2] + l0[2]) * g.h[2] - ats.R[2]), 0.f);
       }
     }
     cnt += __popc(mask);
@@ -264,11 +270,12 @@ __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
 // records: the 64-bit sphere mask skips the points an image does not reach, the table offset
 // of the brick corner locates the point's channel group.
 template <typename Real>
-__global__ void __launch_bounds__(256) k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms,
+__global__ void __launch_bounds__(224, sizeof(Real) == 4 ? 2 : 1) k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms,
                                                 const Real* __restrict__ gdv, const Real* __restrict__ chi,
                                                 const TileEntry* __restrict__ entries, const int* __restrict__ blist,
-                                                const int4* __restrict__ brec, const int* __restrict__ bn,
-                                                const Real* __restrict__ A, Real* __restrict__ W) {
+                                                const int4* __restrict__ brec, const float4* __restrict__ bd0,
+                                                const int* __restrict__ bn, const Real* __restrict__ A,
+                                                Real* __restrict__ W) {
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int o[3];
@@ -287,6 +294,7 @@ __global__ void __launch_bounds__(256) k_wtable(Geo g, Wave w, const AtomTab* __
     const int bx = bi % nbx, by = bi / nbx;
     const int br = (slab * nby + by) * nbx + bx;
     const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
+    const float4* rd = bd0 + ((size_t)tl * g.nbricks + br) * g.br_cap;
     const int* lst = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
     const int nb = bn[(size_t)tl * g.nbricks + br];
     const int bl[3] = {o[0] - g.m[0] + bx * kBrick, o[1] - g.m[1] + by * kBrick, o[2] - g.m[2] + slab * kBrick};
@@ -299,11 +307,22 @@ __global__ void __launch_bounds__(256) k_wtable(Geo g, Wave w, const AtomTab* __
         const int4 r0 = rb[2 * k], r1 = rb[2 * k + 1];
         const unsigned mk = unsigned(half ? r1.w : r1.z) >> pa;   // bits pa + 4 i of this half
         if (!(mk & 0x11111111u)) continue;
-        const TileEntry te = ent[lst[k]];
-        const AtomTab& at = atoms[te.atom];
-        int l0[3];   // box-local lattice coordinates of the brick corner
+        // x - R of the brick corner (FP32 path: from the record; FP64: from the image)
+        int l0[3] = {0, 0, 0};
+        double Ra[3] = {0.0, 0.0, 0.0};
+        float4 dc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (sizeof(Real) == 4) {
+          dc = rd[k];
+        } else {
+          const TileEntry te = ent[lst[k]];
+          const AtomTab& at = atoms[te.atom];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) l0[b] = bl[b] - (at.lo[b] + te.s[b] * g.n[b]);
+          for (int b = 0; b < 3; ++b) {
+            l0[b] = bl[b] - (at.lo[b] + te.s[b] * g.n[b]);   // box-local lattice coordinates of the corner
+            Ra[b] = at.lo[b] * g.h[b] - at.R[b];
+          }
+        }
+        const float dcv[3] = {dc.x, dc.y, dc.z};
         const int nch = r0.w & 0xff, nchp = (r0.w >> 8) & 0xff;
         for (int c0 = 0; c0 < nch; c0 += 4) {
           Real ag[4];
@@ -319,12 +338,12 @@ __global__ void __launch_bounds__(256) k_wtable(Geo g, Wave w, const AtomTab* __
 #pragma unroll
               for (int c = 0; c < 4; ++c) cs += ag[c] * cr[c];
               if (cs == Real(0)) continue;
-              const int l[3] = {l0[0] + pa, l0[1] + pb, l0[2] + pc};
-              // x_b - R_b of the image: l_b h_b + (lo_b h_b - R_b) (the image shift s n h = s L cancels)
+              const int pt[3] = {pa, pb, pc};
+              // x_b - R_b of the image: (l0_b + pt_b) h_b + (lo_b h_b - R_b) (the shift s n h = s L cancels)
 #pragma unroll
               for (int b = 0; b < 3; ++b) {
-                const Real d = (sizeof(Real) == 4) ? Real(l[b]) * hr[b] + Real(at.dlo[b])
-                                                   : Real((at.lo[b] + l[b]) * g.h[b] - at.R[b]);
+                const Real d = (sizeof(Real) == 4) ? Real(dcv[b]) + Real(pt[b]) * hr[b]
+                                                   : Real((l0[b] + pt[b]) * g.h[b] + Ra[b]);
                 acc[i][b] += cs * d;
               }
             }
@@ -368,14 +387,14 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, const Real
                                           h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.slab_n,
-                                                          h->wb.slab_map, h->d.status);
+                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.brick_d0,
+                                                          h->wb.slab_n, h->wb.slab_map, h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
                                           (double*)h->wb.Pg[0], (double*)h->wb.Pg[1]);
   SQ_LAUNCH_CHECK(h);
   k_wtable<Real><<<dim3(g.nslab, w.ntiles), 224, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries, h->wb.brick_list,
-                                                          h->wb.brick_rec, h->wb.brick_n, A, W);
+                                                          h->wb.brick_rec, h->wb.brick_d0, h->wb.brick_n, A, W);
   SQ_LAUNCH_CHECK(h);
   SQ_CUDA_TRY(h, cudaMemsetAsync(T0, 0, sizeof(Real) * (size_t)w.ntiles * g.Upts * g.B, s));
   k_init_t0<Real><<<(w.ntiles + 31) / 32, dim3(g.B, 32), 0, s>>>(g, w, T0);
@@ -389,8 +408,8 @@ int build_wave_entries(sq_handle* h, const Wave& w) {
   k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows, h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.slab_n,
-                                                          h->wb.slab_map, h->d.status);
+                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.brick_d0,
+                                                          h->wb.slab_n, h->wb.slab_map, h->d.status);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }
