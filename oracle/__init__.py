@@ -15,4 +15,5 @@ Modules
                 and the exactly separable truncated region)
   green_kubo    Green-Kubo shear viscosity of a stress time series (Eq. viscosity)
   per_node      the per-node spectral bounds mode (chi_q, zeta_q of each H_q)
+  gauss_sq      Gauss Spectral Quadrature of the density (Lanczos from e_q per node)
 """

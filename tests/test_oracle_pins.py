@@ -11,7 +11,7 @@ import pytest
 import scipy.integrate
 import scipy.linalg
 
-from oracle import dense_k, free_electron, green_kubo, per_node
+from oracle import dense_k, free_electron, gauss_sq, green_kubo, per_node
 from oracle.sq_oracle import (K_PAIRS, NodeRegion, Problem, cheb_coeffs, chebyshev_columns, contract,
                               entropy_fn, fd_coefficients, fd_weights, fermi, fermi_bisect, lanczos_bounds,
                               node_moments, primed, run)
@@ -502,3 +502,48 @@ def test_p12_per_node_mode_reduces_to_shared_mode(per_node_case):
     assert abs(out["F"] - ref["F"]) <= 1e-12 * abs(ref["F"])
     np.testing.assert_allclose(out["sigma"], ref["sigma"], rtol=0, atol=1e-12)
     assert abs(out["N_check"] - inst["n_e"]) < 1e-10 * inst["n_e"]
+
+
+# ---------------------------------------------------------------- P13: Gauss SQ density
+def test_p13_gauss_quadrature_is_exact_to_degree_2k_minus_1():
+    """k-point Gauss quadrature of e_q's spectral measure integrates lambda^p exactly for
+    p <= 2k - 1: sum_i w_i theta_i^p = e_q^T H_q^p e_q (repeated applications of the region
+    operator), and not for p = 2k."""
+    inst = tiny_instance(seed=11, n=(4, 4, 4), h=(0.8, 0.8, 0.8), n_atoms=3, n_o=3, r_cut=2.4, n_pl=12)
+    prob = Problem(inst)
+    region = NodeRegion(prob, prob.node_coords(21))
+    k = 3
+    theta, w = gauss_sq.node_quadrature(prob, 21, k)
+    t = region.unit()
+    e = t.copy()
+    for p in range(0, 2 * k + 1):
+        exact = float(np.sum(e * t))
+        quad = float(np.sum(w * theta ** p))
+        if p <= 2 * k - 1:
+            assert abs(quad - exact) <= 1e-11 * max(1.0, abs(exact)), p
+        else:
+            assert abs(quad - exact) > 1e-6 * abs(exact)
+        t = region.apply_H(t)
+
+
+def test_p13_gauss_full_krylov_equals_dense_and_matches_clenshaw_curtis():
+    """With k = the region dimension the quadrature is [g(H_q)]_qq from a dense eigensolver; on a
+    4^3 cell the Gauss SQ density, electron count and band energy equal the Clenshaw-Curtis SQ
+    ones once both have converged (k = n_pl = 40)."""
+    inst = tiny_instance(seed=2, n=(4, 4, 4), h=(0.8, 0.8, 0.8), n_atoms=2, n_o=1, r_cut=0.9, n_pl=10)
+    prob = Problem(inst)
+    region = NodeRegion(prob, prob.node_coords(5))
+    Hd = region.dense_H()
+    ev, U = np.linalg.eigh(Hd)
+    c = np.ravel_multi_index(region.center, region.shape)
+    theta, w = gauss_sq.node_quadrature(prob, 5, Hd.shape[0])
+    mu = 2.0
+    dense = float(np.sum(U[c, :] ** 2 * fermi((ev - mu) / prob.kT)))
+    assert abs(float(np.sum(w * fermi((theta - mu) / prob.kT))) - dense) <= 1e-12
+    inst = tiny_instance(seed=11, n=(4, 4, 4), h=(0.8, 0.8, 0.8), n_atoms=3, n_o=3, r_cut=2.4, n_pl=40)
+    g = gauss_sq.run(inst, k=40)
+    cc = run(inst, bounds=lanczos_bounds(Problem(inst)))
+    assert abs(g["mu"] - cc["mu"]) <= 1e-11 * abs(cc["mu"])
+    assert np.abs(g["rho"] - cc["rho"]).max() <= 1e-11 * np.abs(cc["rho"]).max()
+    assert abs(g["E_band"] - cc["E_band"]) <= 1e-11 * abs(cc["E_band"])
+    assert abs(g["N_check"] - inst["n_e"]) <= 1e-11 * inst["n_e"]
