@@ -211,6 +211,35 @@ def test_config4_largest_window_sampled_nodes(sq, config4_large_setup, precision
     assert np.all(np.isfinite(sig)) and np.all(np.diag(sig) < 0.0)
 
 
+def test_config4_512_atoms_mixed(sq):
+    """The largest batched snapshot: 512 H on an 80^3 grid (m = 11, n_pl = 75; about 31 GB on
+    the device, several waves of tiles) in mixed precision with given bounds: the density at
+    sampled nodes at a test-chosen mu against the oracle (computed node by node), and the
+    electron count at the Fermi level."""
+    inst = make_batch(4, count=1, atom_choices=(512,))[0]
+    prob = orc.Problem(inst)
+    assert list(prob.n) == [80, 80, 80] and list(prob.m) == [11, 11, 11] and prob.n_pl == 75
+    bounds = (-5.0, 130.0)
+    nodes = [0, 80 ** 3 // 2 + 37, 80 ** 3 - 1]
+    ref = orc.all_moments(prob, *bounds, nodes=nodes)
+    nd = 80 ** 3
+    h = sq.sq_setup(sq.Desc(inst, sq.SQ_MIXED, bounds=bounds))
+    try:
+        sq.sq_moments(h)
+        mu = -8.5
+        rho, en, sig = sq.sq_density_energy_stress(h, mu, nd)
+        c, _, _ = orc.fd_coefficients(mu, prob.kT, 0.5 * (bounds[1] + bounds[0]), 0.5 * (bounds[1] - bounds[0]),
+                                      prob.n_pl, prob.M)
+        rho_ref = 2.0 / prob.dV * (ref[:, :, 0] @ (orc.primed(prob.n_pl) * c))
+        assert np.abs(rho[nodes] - rho_ref).max() <= 2e-5 * np.abs(rho_ref).max()
+        mu = sq.sq_fermi_level(h)
+        rho, en, sig = sq.sq_density_energy_stress(h, mu, nd)
+    finally:
+        sq.sq_destroy(h)
+    assert abs(en["N_check"] - inst["n_e"]) <= 1e-9 * inst["n_e"]
+    assert np.all(np.isfinite(sig)) and np.all(np.diag(sig) < 0.0)
+
+
 def test_call_order_errors(sq):
     inst = tiny_instance(**TINY["m1_no1"])
     d = sq.Desc(inst, sq.SQ_FP64, bounds=(-2.0, 20.0))
