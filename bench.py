@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-requests", type=int, default=8,
                     help="requests in the served-stream measurement (0 disables it)")
+    ap.add_argument("--batch", type=int, default=6,
+                    help="instances in the batched-snapshot measurement (0 disables it)")
     ap.add_argument("--profile-case", action="store_true",
                     help="only run two sweeps of the small profiling case (16^3 cell at the 40^3 "
                          "workload's parameters and atom density) for a profiler capture; prints no bench line")
@@ -238,6 +240,37 @@ def serve_stream(sq, n_req: int, prec: int):
                         "[1.6, 6.3], n_pl in [30, 80], R_cut in [3, 5]), Poisson arrivals"}
 
 
+def batch_throughput(sq, prec: int, count: int = 6, concurrent: int = 3):
+    """A batch of uneven snapshots of the batched workload (32 / 64 / 128-atom cells with their
+    own grid, kT, n_pl and R_cut) evaluated together by sq_batch_evaluate (each on its own stream,
+    `concurrent` at a time): evaluations/s and region point-steps/s of the whole batch."""
+    import numpy as np
+    import torch
+    from workloads import make_batch
+    insts = make_batch(config=4, count=count, atom_choices=(32, 64, 128))
+    streams = [torch.cuda.Stream() for _ in insts]
+    hs = [sq.sq_setup(sq.Desc(inst, prec, bounds=None, stream=st.cuda_stream)) for inst, st in zip(insts, streams)]
+    point_steps = 0.0
+    for inst in insts:
+        m = np.floor(float(inst["r_cut"]) / (np.asarray(inst["L"]) / np.asarray(inst["n"])) + 1e-9)
+        point_steps += float(np.prod(inst["n"])) * float(np.prod(2 * m + 1)) * float(inst["n_pl"])
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mu, en, sig = sq.sq_batch_evaluate(hs, max_concurrent=concurrent)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    finally:
+        for h in hs:
+            sq.sq_destroy(h)
+    return {"instances": count, "concurrent": concurrent, "evals_per_s": count / wall, "wall_s": wall,
+            "point_steps_per_s": point_steps / wall,
+            "atoms": [int(len(i["pos"])) for i in insts], "n_pl": [int(i["n_pl"]) for i in insts],
+            "ok": bool(all(abs(e["N_check"] - i["n_e"]) <= 1e-8 * i["n_e"] for e, i in zip(en, insts))),
+            "workload": "uneven snapshots of the batched config (32/64/128 H at 0.0375 / bohr^3, h = 0.3, "
+                        "kT in [1.6, 6.3], n_pl in [30, 80], R_cut in [3, 5]), device Lanczos bounds"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -409,6 +442,8 @@ def run_ours(args):
     sq.sq_destroy(h)
     if rank == 0 and args.serve_requests > 0:
         line["serving"] = serve_stream(sq, args.serve_requests, prec)
+    if rank == 0 and args.batch > 0:
+        line["batch"] = batch_throughput(sq, prec, count=args.batch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(inst, args.cpu_seconds)
     if rank == 0:
