@@ -241,6 +241,20 @@ int sq_server_pending(sq_server* s);
  * polled are dropped). */
 void sq_server_destroy(sq_server* s);
 
+/* Gauss Spectral Quadrature of the electron density (the SQ variant the paper uses for the SCF
+ * density, Sec. 5; cited there without formulas). For every node q: k-step Lanczos on H_q from
+ * the node's unit vector e_q (classical Gram-Schmidt applied twice, as for the spectral bounds;
+ * FP32 vectors in SQ_MIXED), the eigenvalues theta_qi and squared first eigenvector components
+ * w_qi of its tridiagonal (k-point Gauss quadrature of e_q's spectral measure, exact for
+ * polynomials of degree <= 2k - 1); rho_q = (2/|dOmega|) sum_i w_qi g(theta_qi) with the Fermi
+ * level from 2 sum_q sum_i w_qi g(theta_qi) = N_e (the bisection rule of sq_fermi_level) and
+ * E_band = 2 sum_q sum_i w_qi theta_qi g(theta_qi). Independent of sq_moments (it neither needs
+ * nor changes the Chebyshev moments; it rebuilds the per-wave lists). k in 1..128 (capped at
+ * the region dimension). Host outputs: mu_out, rho_out [N_d] (x fastest), e_band_out, each may
+ * be NULL. Allocates and frees its own device scratch; synchronises the stream.
+ * Errors: SQ_ERR_INVALID_ARG (k), SQ_ERR_OOM, SQ_ERR_NO_BRACKET, SQ_ERR_CUDA. */
+int sq_gauss_density(sq_handle* h, int k, double* mu_out, double* rho_out, double* e_band_out);
+
 /* Green-Kubo shear viscosity (Sec. 5.2, Eq. viscosity) of a stress time series, e.g. the sigma
  * of successive snapshots of a trajectory served through sq_server_*:
  *   eta(k dt) = |Omega| / kT * int_0^{k dt} (1/5) sum_i <s_i(t') s_i(0)> dt',

@@ -222,10 +222,13 @@ int build_wave_entries(sq_handle* h, const Wave& w);
 
 // bounds / Fermi level / contraction (sq_reduce.cu)
 int run_lanczos(sq_handle* h);
+// k-step Lanczos of every node column of a wave (start 0: hash vector, 1: e_q); see sq_lanczos.cu
+template <typename Real>
+int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C);
 int run_fermi(sq_handle* h, double* mu_out);
 int run_contraction(sq_handle* h, double mu, double* rho_dev, double* sums_host);
 
 // status word indices
-enum StatusWord { kStOverflow = 0, kStNoBracket = 1, kStTimeout = 2, kStCount = 4 };
+enum StatusWord { kStOverflow = 0, kStNoBracket = 1, kStTimeout = 2, kStNoConverge = 3, kStCount = 4 };
 
 }  // namespace sq

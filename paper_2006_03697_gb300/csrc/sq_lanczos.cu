@@ -44,6 +44,24 @@ __global__ void k_lz_init(Geo g, Wave w, Real* __restrict__ V0) {
   }
 }
 
+// Start vector e_q: one at node q's own point of the union window, zero elsewhere (and an
+// all-zero column for padding nodes, which the mark-empty pass then skips).
+template <typename Real>
+__global__ void k_lz_init_unit(Geo g, Wave w, Real* __restrict__ V0) {
+  const size_t per_tile = (size_t)g.Upts * g.B;
+  const size_t total = per_tile * w.ntiles;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int tl = int(idx / per_tile);
+    const int r = int(idx % per_tile);
+    const int q = r % g.B, pt = r / g.B;
+    int o[3], qo[3];
+    tile_origin(g, wave_tile(w, tl), o);
+    node_offset(g, q, qo);
+    const int cpt = ((qo[2] + g.m[2]) * g.U[1] + (qo[1] + g.m[1])) * g.U[0] + (qo[0] + g.m[0]);
+    V0[idx] = (node_valid(g, o, qo) && pt == cpt) ? Real(1) : Real(0);
+  }
+}
+
 // out[col * ld + i] = <V_i, x>_col for i < nvec (one block per (i, tile); fixed-order sums:
 // per thread in the vectors' precision, across threads in FP64)
 template <typename Real>
@@ -212,22 +230,22 @@ __global__ void k_lz_bounds(int ncols, int k, const double* __restrict__ alpha, 
   }
 }
 
+// k-step Lanczos (CGS2 reorthogonalisation) of every node column of the wave's tiles, from the
+// hash start vector (start = 0, the spectral bounds) or from e_q (start = 1, Gauss SQ). V holds
+// k + 1 vectors of the wave, W one, P the projections; C is (5 k + 8) doubles per column:
+// cA, cB, nrm [ncols][k + 1], alpha, beta [ncols][k], keff (ints) - see lz_alpha etc.
 template <typename Real>
-static int run_lanczos_t(sq_handle* h) {
+int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  const int nst = int(h->lanczos_tiles.size());
-  const int k = h->lanczos_k;
+  const int nst = w.ntiles;
   // never more steps than the region has dimensions (the Krylov space is exhausted)
   const long long nc = (long long)(2 * g.m[0] + 1) * (2 * g.m[1] + 1) * (2 * g.m[2] + 1);
   const int kk = int(std::min<long long>(k, nc));
   const int ncols = nst * g.B;
   const int ld = k + 1;
-  const Wave w{0, nst, h->d.lz_tiles};
   const size_t vstride = (size_t)nst * g.Upts * g.B;
-  Real* V = reinterpret_cast<Real*>(h->d.lzV);   // buffers sized for FP64
-  Real* W = reinterpret_cast<Real*>(h->d.lzW);
-  double* cA = h->d.lzC;
+  double* cA = C;
   double* cB = cA + (size_t)ncols * ld;
   double* nrm = cB + (size_t)ncols * ld;
   double* alpha = nrm + (size_t)ncols * ld;
@@ -238,7 +256,8 @@ static int run_lanczos_t(sq_handle* h) {
   const int cb = (ncols + 127) / 128;
   int rc = build_wave_entries(h, w);
   if (rc != SQ_OK) return rc;
-  k_lz_init<Real><<<eb, 256, 0, s>>>(g, w, V);
+  if (start == 0) k_lz_init<Real><<<eb, 256, 0, s>>>(g, w, V);
+  else k_lz_init_unit<Real><<<eb, 256, 0, s>>>(g, w, V);
   SQ_LAUNCH_CHECK(h);
   k_lz_dots<Real><<<dim3(1, nst), kThreads, 0, s>>>(g, w, V, 1, vstride, V, nrm, ld);
   SQ_LAUNCH_CHECK(h);
@@ -248,7 +267,7 @@ static int run_lanczos_t(sq_handle* h) {
   SQ_LAUNCH_CHECK(h);
   for (int i = 0; i < kk; ++i) {
     Real* Vi = V + (size_t)i * vstride;
-    rc = launch_apply_h(h, w, Vi, W, reinterpret_cast<Real*>(h->d.lzP));
+    rc = launch_apply_h(h, w, Vi, W, P);
     if (rc != SQ_OK) return rc;
     k_lz_dots<Real><<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cA, ld);
     SQ_LAUNCH_CHECK(h);
@@ -267,6 +286,25 @@ static int run_lanczos_t(sq_handle* h) {
       SQ_LAUNCH_CHECK(h);
     }
   }
+  return SQ_OK;
+}
+
+template int lanczos_columns<float>(sq_handle*, const Wave&, int, int, float*, float*, float*, double*);
+template int lanczos_columns<double>(sq_handle*, const Wave&, int, int, double*, double*, double*, double*);
+
+template <typename Real>
+static int run_lanczos_t(sq_handle* h) {
+  const int nst = int(h->lanczos_tiles.size());
+  const int k = h->lanczos_k;
+  const int ncols = nst * h->geo.B;
+  const Wave w{0, nst, h->d.lz_tiles};
+  int rc = lanczos_columns<Real>(h, w, 0, k, reinterpret_cast<Real*>(h->d.lzV), reinterpret_cast<Real*>(h->d.lzW),
+                                 reinterpret_cast<Real*>(h->d.lzP), h->d.lzC);
+  if (rc != SQ_OK) return rc;
+  const double* alpha = h->d.lzC + (size_t)3 * ncols * (k + 1);
+  const double* beta = alpha + (size_t)ncols * k;
+  const int* keff = (const int*)(beta + (size_t)ncols * k);
+  cudaStream_t s = h->stream;
   k_lz_bounds<<<1, 256, 0, s>>>(ncols, k, alpha, beta, keff, h->d.scal);
   SQ_LAUNCH_CHECK(h);
   double b2[2];

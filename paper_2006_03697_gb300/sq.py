@@ -30,7 +30,8 @@ EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
     "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit",
-    "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_green_kubo", "sq_destroy", "sq_last_error",
+    "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_gauss_density", "sq_green_kubo", "sq_destroy",
+    "sq_last_error",
 ]
 SQ_K_STENCIL = 0
 SQ_K_PROJECT = 1
@@ -113,6 +114,8 @@ def lib():
         L.sq_server_pending.restype = C.c_int
         L.sq_server_destroy.argtypes = [C.c_void_p]
         L.sq_server_destroy.restype = None
+        L.sq_gauss_density.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_double)]
+        L.sq_gauss_density.restype = C.c_int
         L.sq_green_kubo.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
                                     C.c_void_p, C.c_void_p, C.c_void_p]
         L.sq_green_kubo.restype = C.c_int
@@ -300,6 +303,14 @@ def sq_batch_evaluate(handles, max_concurrent: int = 0):
         raise SQError(rc, "sq_batch_evaluate failed (see the handles' sq_last_error)")
     energies = [{k: getattr(en[i], k) for k, _ in sq_energies._fields_} for i in range(n)]
     return mu, energies, sig.reshape(n, 3, 3)
+
+
+def sq_gauss_density(h, k: int, nd: int):
+    """Gauss SQ density: (mu, rho (N_d,), E_band)."""
+    mu, eb = C.c_double(), C.c_double()
+    rho = np.zeros(nd)
+    _check(lib().sq_gauss_density(h, int(k), C.byref(mu), rho.ctypes.data, C.byref(eb)), h)
+    return mu.value, rho, eb.value
 
 
 def sq_green_kubo(sigma, dt: float, volume: float, kT: float, max_lag: int, stream=None):
