@@ -190,7 +190,8 @@ static int gauss_t(sq_handle* h, int k, double* mu_out, double* rho_host, double
     return fail(h, SQ_ERR_OOM, "device allocation for the Gauss quadrature failed");
   }
   int rc = SQ_OK;
-  SQ_CUDA_TRY(h, cudaMemsetAsync(h->d.status, 0, sizeof(int) * kStCount, s));
+  if (cudaMemsetAsync(h->d.status, 0, sizeof(int) * kStCount, s) != cudaSuccess)
+    rc = fail(h, SQ_ERR_CUDA, "status reset failed");
   for (int t0 = 0; t0 < g.n_tiles && rc == SQ_OK; t0 += wt) {
     const Wave w{t0, std::min(wt, g.n_tiles - t0), nullptr};
     rc = lanczos_columns<Real>(h, w, 1, k, V, W, P, C);

@@ -69,6 +69,8 @@ def test_null_handle_calls_are_rejected(sq):
     L = sq.lib()
     assert L.sq_moments(None) == sq.SQ_ERR_INVALID_ARG
     assert L.sq_fermi_level(None, None) == sq.SQ_ERR_INVALID_ARG
+    assert L.sq_pressure(None, 0.0, None, None) == sq.SQ_ERR_INVALID_ARG
+    assert L.sq_gauss_density(None, 20, None, None, None) == sq.SQ_ERR_INVALID_ARG
     assert L.sq_kernel_launches(None) == 0
     L.sq_destroy(None)
 
