@@ -3,7 +3,8 @@
  * library: electron density, band / entropy / nonlocal energies and the density-matrix
  * (kinetic + nonlocal) Hellmann-Feynman stress of an orthorhombic periodic cell, following
  * Sharma, Hamel, Bethkenhagen, Pask, Suryanarayana, "Real-space formulation of the stress
- * tensor for O(N) density functional theory" (arXiv 2006.03697), Sec. 4 and App. A.
+ * tensor for O(N) density functional theory" (arXiv 2006.03697), Sec. 4 and App. A; also the
+ * Gauss SQ density and the Green-Kubo viscosity the paper uses in Sec. 5.
  *
  * Problem statement (Sec. 4). The cell is discretised by a uniform grid K_Omega of N_d nodes,
  * node i at (ix h0, iy h1, iz h2), h_a = L_a / n_a. For every node q the nodal Hamiltonian
@@ -57,8 +58,10 @@ extern "C" {
 
 /* precision modes */
 #define SQ_FP64 0    /* FP64 recurrence, projectors and moments                          */
-#define SQ_MIXED 1   /* FP32 recurrence / projectors / moment products, FP64 node sums,
-                        FP64 bounds, coefficients, bisection and contraction            */
+#define SQ_MIXED 1   /* FP32 recurrence and moment products, projector products on TF32
+                        tensor cores with a hi/lo split (about 2^-21 relative), FP32
+                        Lanczos vectors for the bounds; FP64 node and cross-thread sums,
+                        Gram-Schmidt coefficients, Fermi search and contraction          */
 
 /* spectral bound modes (the paper takes chi, zeta from the extreme eigenvalues of H_q) */
 #define SQ_BOUNDS_LANCZOS 0   /* k-step Lanczos on sample regions, widened (default)   */
