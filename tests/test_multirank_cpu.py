@@ -45,3 +45,16 @@ def test_max_over_ranks_and_rate_gloo():
 def test_single_process_passthrough():
     import bench
     assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
+
+
+def test_stencil_traffic_figure_is_tied_to_the_profiled_kernel_text():
+    """bench.py reports the committed ncu DRAM traffic only for the step-kernel source it was
+    captured on (keyed by a hash of that text), else null."""
+    import json
+    import os
+    import bench
+    path = os.path.join(os.path.dirname(os.path.abspath(bench.__file__)), "profiles", "stencil_traffic.json")
+    t = json.load(open(path))
+    assert bench.stencil_traffic(t["step_kernel_sha1"]) == float(t["bytes_per_launch_full_size"])
+    assert bench.stencil_traffic("0" * 40) is None
+    assert len(bench.step_kernel_hash()) == 40
