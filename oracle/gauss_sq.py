@@ -20,19 +20,25 @@ import scipy.linalg
 from .sq_oracle import NodeRegion, Problem, fermi
 
 
-def lanczos_tridiagonal(apply, v0: np.ndarray, k: int):
-    """(alpha, beta) of k-step Lanczos from v0 (normalised), CGS2 reorthogonalisation; stops
-    early when beta <= 1e-12 max(1, |alpha|) (the Krylov space is exhausted)."""
+def lanczos_tridiagonal(apply, v0: np.ndarray, k: int, reorth: bool = True):
+    """(alpha, beta) of k-step Lanczos from v0 (normalised); stops early when
+    beta <= 1e-12 max(1, |alpha|) (the Krylov space is exhausted). reorth: full
+    reorthogonalisation by classical Gram-Schmidt applied twice; otherwise the plain three-term
+    recurrence w = H v_i - alpha_i v_i - beta_{i-1} v_{i-1}, alpha_i = v_i^T H v_i."""
     V = [v0 / np.linalg.norm(v0)]
     alpha, beta = [], []
     for i in range(k):
         w = apply(V[i])
-        Vm = np.array(V)
-        c1 = Vm @ w
-        w = w - Vm.T @ c1
-        c2 = Vm @ w
-        w = w - Vm.T @ c2
-        a = float(c1[i] + c2[i])
+        if reorth:
+            Vm = np.array(V)
+            c1 = Vm @ w
+            w = w - Vm.T @ c1
+            c2 = Vm @ w
+            w = w - Vm.T @ c2
+            a = float(c1[i] + c2[i])
+        else:
+            a = float(V[i] @ w)
+            w = w - a * V[i] - (beta[i - 1] * V[i - 1] if i > 0 else 0.0)
         b = float(np.linalg.norm(w))
         alpha.append(a)
         if i == k - 1 or b <= 1e-12 * max(1.0, abs(a)):
@@ -42,13 +48,13 @@ def lanczos_tridiagonal(apply, v0: np.ndarray, k: int):
     return np.array(alpha), np.array(beta)
 
 
-def node_quadrature(prob: Problem, q: int, k: int):
+def node_quadrature(prob: Problem, q: int, k: int, reorth: bool = True):
     """Gauss nodes theta_qi and weights w_qi of node q (k-step Lanczos from e_q)."""
     region = NodeRegion(prob, prob.node_coords(q))
     shape = region.shape
     e = region.unit().reshape(-1)
     alpha, beta = lanczos_tridiagonal(lambda x: region.apply_H(x.reshape(shape)).reshape(-1), e,
-                                      min(k, e.size))
+                                      min(k, e.size), reorth)
     theta, Y = scipy.linalg.eigh_tridiagonal(alpha, beta)
     return theta, Y[0, :] ** 2
 
@@ -73,10 +79,10 @@ def fermi_bisect(prob: Problem, quad) -> float:
     return 0.5 * (lo + hi)
 
 
-def run(inst: dict, k: int = 40):
+def run(inst: dict, k: int = 40, reorth: bool = True):
     """Gauss SQ density, Fermi level and band energy of one instance."""
     prob = Problem(inst)
-    quad = [node_quadrature(prob, q, k) for q in range(prob.Nd)]
+    quad = [node_quadrature(prob, q, k, reorth) for q in range(prob.Nd)]
     mu = fermi_bisect(prob, quad)
     g = [w * fermi((t - mu) / prob.kT) for t, w in quad]
     rho = np.array([2.0 / prob.dV * float(np.sum(gi)) for gi in g])

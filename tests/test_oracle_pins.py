@@ -564,3 +564,24 @@ def test_p11_green_kubo_autocorrelation_equals_wiener_khinchin():
     raw = np.fft.irfft(spec * np.conj(spec), n=2 * n, axis=1)[:, : max_lag + 1, :]   # sum over origins
     wk = raw.sum(axis=(0, 2)) / (5.0 * s.shape[0] * (n - np.arange(max_lag + 1)))
     np.testing.assert_allclose(c, wk, rtol=1e-10, atol=1e-13)
+
+
+def test_p13_gauss_plain_lanczos_matches_reorthogonalised():
+    """The plain three-term Lanczos recurrence (no reorthogonalisation) gives the same Gauss
+    rule to rounding: exact to degree 2k - 1 at small k and the same density, Fermi level and
+    band energy as the reorthogonalised run once converged (k = 40)."""
+    inst = tiny_instance(seed=11, n=(4, 4, 4), h=(0.8, 0.8, 0.8), n_atoms=3, n_o=3, r_cut=2.4, n_pl=40)
+    prob = Problem(inst)
+    theta, w = gauss_sq.node_quadrature(prob, 21, 3, reorth=False)
+    region = NodeRegion(prob, prob.node_coords(21))
+    t = region.unit()
+    e = t.copy()
+    for p in range(0, 6):
+        exact = float(np.sum(e * t))
+        assert abs(float(np.sum(w * theta ** p)) - exact) <= 1e-11 * max(1.0, abs(exact)), p
+        t = region.apply_H(t)
+    a = gauss_sq.run(inst, k=40)
+    b = gauss_sq.run(inst, k=40, reorth=False)
+    assert abs(a["mu"] - b["mu"]) <= 1e-12 * abs(a["mu"])
+    assert np.abs(a["rho"] - b["rho"]).max() <= 1e-12 * np.abs(a["rho"]).max()
+    assert abs(a["E_band"] - b["E_band"]) <= 1e-12 * abs(a["E_band"])
