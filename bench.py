@@ -12,8 +12,10 @@ and the contraction into rho, energies and sigma - every row of the hot path.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference    # the FP64 CPU oracle on the host cores
 
-With N > 1 (torchrun) every rank evaluates its own snapshot (independent instances, no
-data-path collective): weak scaling, value = all ranks' evaluations / max-rank time.
+With N > 1 (torchrun, or --gpus N, which starts the N ranks itself) the instance is split
+by the node partition: each rank sweeps an equal contiguous range of the node tiles, one NCCL
+allreduce of the node sums R^j precedes the Fermi search and one of the energy / stress
+partials follows the contraction. Strong scaling: value = whole-cell evaluations / max-rank time.
 """
 from __future__ import annotations
 
@@ -45,7 +47,12 @@ def parse():
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
                     help="skip timing one FP64 evaluation (the plain FP64 GPU path) on the same input")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-nodes", type=int, default=416,
+                    help="seeded node columns in the oracle sample of cpu_baseline")
+    ap.add_argument("--cpu-nodes-per-step", type=int, default=64,
+                    help="seeded node columns per step of --impl reference")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed evaluations of the plain FP64 GPU path (after one warm-up)")
     ap.add_argument("--serve-requests", type=int, default=8,
                     help="requests in the served-stream measurement (0 disables it)")
     ap.add_argument("--batch", type=int, default=6,
@@ -160,41 +167,72 @@ def stencil_traffic(sweep_hash: str):
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-def _oracle_nodes(args):
-    inst, nodes, lo, hi = args
+_ORACLE = {}
+
+
+def _oracle_init(inst, lo, hi):
+    """Pool initializer: each worker builds the oracle's problem once (outside any timing)."""
     from oracle import sq_oracle as orc
-    prob = orc.Problem(inst)
-    t0 = time.perf_counter()
+    _ORACLE["orc"] = orc
+    _ORACLE["prob"] = orc.Problem(inst)
+    _ORACLE["bounds"] = (lo, hi)
+
+
+def _oracle_nodes(nodes):
+    orc, prob = _ORACLE["orc"], _ORACLE["prob"]
+    lo, hi = _ORACLE["bounds"]
     for q in nodes:
         orc.node_moments(prob, prob.node_coords(q), lo, hi)
-    return time.perf_counter() - t0
+    return len(nodes)
 
 
-def cpu_oracle_rate(inst, seconds: float):
-    """The oracle as it stands, node by node on all host cores (spawn pool): evaluations/s
-    extrapolated from a bounded sample of nodes (per-node moments dominate its cost)."""
-    import multiprocessing as mp
-    import numpy as np
-    from oracle import sq_oracle as orc
-    prob = orc.Problem(inst)
-    lo, hi = -6.0, 130.0
-    cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    orc.node_moments(prob, prob.node_coords(0), lo, hi)
-    per_node = time.perf_counter() - t0
-    per_worker = max(1, int(seconds / max(per_node, 1e-3)))
-    rng = np.random.Generator(np.random.PCG64(12345))
-    nodes = rng.choice(prob.Nd, size=min(prob.Nd, per_worker * cores), replace=False).tolist()
-    chunks = [nodes[i::cores] for i in range(cores)]
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(cores) as pool:
-        pool.map(_oracle_nodes, [(inst, ch, lo, hi) for ch in chunks if ch])
-    wall = time.perf_counter() - t0
-    nodes_per_s = len(nodes) / wall
-    return {"value": nodes_per_s / prob.Nd, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{len(nodes)} of {prob.Nd} node columns (moments, n_pl={prob.n_pl}) in {wall:.1f} s "
-                      f"on {cores} processes; Fermi search and contraction (O(N_d n_pl)) not timed",
-            "nodes_per_s": nodes_per_s}
+class OracleTimer:
+    """The FP64 CPU oracle as it stands, node column by node column on every host core.
+
+    A spawn pool is started and each worker builds the problem before anything is timed; a
+    timed sample is a fixed, seeded set of node columns (their per-node moments dominate the
+    oracle's cost; the Fermi search and contraction are O(N_d n_pl) and not timed). The rate is
+    extrapolated to whole evaluations: evals/s = (node columns/s) / N_d."""
+
+    BOUNDS = (-6.0, 130.0)
+
+    def __init__(self, inst):
+        import multiprocessing as mp
+        import numpy as np
+        self.nd = int(np.prod(inst["n"]))
+        self.n_pl = int(inst["n_pl"])
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
+                                                 initargs=(inst,) + self.BOUNDS)
+        self.pool.map(_oracle_nodes, [[] for _ in range(self.cores)])   # workers started and ready
+        self.rng = np.random.Generator(np.random.PCG64(12345))
+
+    def sample(self, n_nodes: int):
+        nodes = self.rng.choice(self.nd, size=min(self.nd, n_nodes), replace=False).tolist()
+        chunks = [nodes[i::self.cores] for i in range(self.cores)]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_nodes, [c for c in chunks if c])
+        wall = time.perf_counter() - t0
+        nodes_per_s = len(nodes) / wall
+        return {"value": nodes_per_s / self.nd, "unit": METRIC, "cores": self.cores, "kind": "oracle",
+                "sample": f"{len(nodes)} seeded node columns of {self.nd} (per-node moments, n_pl={self.n_pl}) in "
+                          f"{wall:.1f} s on {self.cores} worker processes; scaled by N_d / sample = "
+                          f"{self.nd / len(nodes):.0f}; Fermi search and contraction (O(N_d n_pl)) not timed",
+                "nodes_per_s": nodes_per_s, "sample_nodes": len(nodes), "extrapolation": self.nd / len(nodes),
+                "wall_s": wall}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_rate(inst, n_nodes: int):
+    """One bounded sample (n_nodes seeded node columns) of the oracle on all host cores."""
+    timer = OracleTimer(inst)
+    try:
+        return timer.sample(n_nodes)
+    finally:
+        timer.close()
 
 
 def serve_stream(sq, n_req: int, prec: int):
@@ -272,26 +310,37 @@ def batch_throughput(sq, prec: int, count: int = 6, concurrent: int = 3):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: W untimed samples, then K timed samples of
+    --cpu-nodes-per-step seeded node columns each (the pool is started before the warm-up)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from workloads import make_instance
     inst = make_instance(args.config)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        cpu_oracle_rate(inst, 1.0)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_oracle_rate(inst, max(1.0, args.cpu_seconds / max(1, args.steps))))
-    wall = time.perf_counter() - t0
-    v = sum(x["value"] for x in vals) / len(vals)
+    timer = OracleTimer(inst)
+    try:
+        for _ in range(args.warmup):
+            timer.sample(timer.cores)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(timer.sample(args.cpu_nodes_per_step))
+        wall = time.perf_counter() - t0
+    finally:
+        timer.close()
+    nodes = sum(x["sample_nodes"] for x in vals)
+    node_s = sum(x["wall_s"] for x in vals)
+    v = nodes / node_s / timer.nd
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": CONFIG_NAME, "flush_l2": "working set > L2 (CPU run)"},
-        "cpu_baseline": {"value": v, "unit": METRIC, "cores": vals[0]["cores"], "kind": "oracle",
-                         "sample": vals[0]["sample"]},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": timer.cores, "kind": "oracle",
+                         "sample": f"{args.steps} samples of {args.cpu_nodes_per_step} seeded node columns of "
+                                   f"{timer.nd} ({nodes} in {node_s:.1f} s on {timer.cores} worker processes), "
+                                   f"scaled by N_d; Fermi search and contraction not timed",
+                         "nodes_per_s": nodes / node_s},
         "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }
@@ -333,20 +382,43 @@ def run_ours(args):
     from paper_2006_03697_gb300 import sq
     from workloads import make_instance
 
-    inst = make_instance(args.config, instance=rank)
+    # one instance; with N ranks each sweeps its part of the node tiles (the node partition)
+    inst = make_instance(args.config)
     nd = int(np.prod(inst["n"]))
+    n_pl = int(inst["n_pl"])
     prec = sq.SQ_MIXED if args.precision == "mixed" else sq.SQ_FP64
     stream = torch.cuda.Stream()
     sptr = stream.cuda_stream
-    desc = sq.Desc(inst, prec, bounds=None, stream=sptr)
+    part = (rank, world) if world > 1 else None
+    desc = sq.Desc(inst, prec, bounds=None, stream=sptr, partition=part)
     h = sq.sq_setup(desc)
     rho_dev = torch.empty(nd, dtype=torch.float64, device="cuda")
     sig_dev = torch.empty(9, dtype=torch.float64, device="cuda")
 
+    def allreduce(vec):
+        """Sum of a float64 host vector over the ranks (NCCL)."""
+        t = torch.from_numpy(np.ascontiguousarray(vec, dtype=np.float64)).cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t.cpu().numpy()
+
+    def finish(hh, mu, en):
+        """Whole-cell results of a partitioned handle: the parts' sums (one allreduce)."""
+        keys = ("E_band", "E_s", "E_nl", "N_check")
+        tot = allreduce(np.concatenate([[en[k] for k in keys], sig_dev.cpu().numpy()]))
+        out = {k: float(tot[i]) for i, k in enumerate(keys)}
+        out["F"] = out["E_band"] + out["E_s"]
+        out["mu"] = mu
+        sig_dev.copy_(torch.from_numpy(tot[len(keys):]))
+        return out
+
     def step():
         sq.sq_moments(h)
-        mu = sq.sq_fermi_level(h)
-        return sq.sq_density_energy_stress_dev(h, mu, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
+        if dist is None:
+            mu = sq.sq_fermi_level(h)
+            return sq.sq_density_energy_stress_dev(h, mu, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
+        mu = sq.sq_fermi_level_sums(h, allreduce(sq.sq_node_sums(h, n_pl)))   # exchange of R^j
+        en = sq.sq_density_energy_stress_dev(h, mu, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
+        return finish(h, mu, en)
 
     for _ in range(args.warmup):
         en = step()
@@ -376,7 +448,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
-    value = whole_job_rate(world, args.steps, ms)
+    # one instance per step whatever N is (strong scaling): evaluations of the whole cell / s
+    value = whole_job_rate(1, args.steps, ms)
 
     # e2e: the public C ABI from host buffers, setup copies and host outputs inside the region
     rho_h = np.zeros(nd)
@@ -389,13 +462,18 @@ def run_ours(args):
     for _ in range(args.steps):
         hh = sq.sq_setup(desc)
         sq.sq_moments(hh)
-        mu = sq.sq_fermi_level(hh)
+        if dist is None:
+            mu = sq.sq_fermi_level(hh)
+        else:
+            mu = sq.sq_fermi_level_sums(hh, allreduce(sq.sq_node_sums(hh, n_pl)))
         rho_h, en2, sig_h = sq.sq_density_energy_stress(hh, mu, nd)
+        if dist is not None:
+            allreduce(np.concatenate([[en2[k] for k in ("E_band", "E_s", "E_nl", "N_check")], sig_h.reshape(9)]))
         sq.sq_destroy(hh)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
-    e2e = {"value": world * args.steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": args.steps / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h)}
 
     # roofline of the dominant sweep kernel
@@ -412,9 +490,11 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32" if prec == sq.SQ_MIXED else "f64", "data": "synthetic",
         "config": {"workload": CONFIG_NAME, "precision": args.precision, "bounds": "lanczos (device, per step)",
+                   "parallelism": f"node partition over {world} GPU(s): tile ranges, allreduce of R^j and of the "
+                                  "energy / stress partials" if world > 1 else "1 GPU",
                    "node_columns_per_step": nd,
                    "flush_l2": f"no flush: device working set {sq.sq_footprint_bytes(desc) / 1e9:.1f} GB > L2"},
         "node_columns_per_s": value * nd,
@@ -423,29 +503,43 @@ def run_ours(args):
         "sigma": sig_dev.cpu().numpy().reshape(3, 3).tolist(),
         "pressure_app_a": sq.sq_pressure(h, en["mu"])[0],
     }
-    if args.fp64_compare and rank == 0:
+    if args.fp64_compare and rank == 0 and world == 1:
+        # the plain FP64 GPU path (same library, SQ_FP64) on the same input: one untimed warm-up
+        # evaluation, then --fp64-steps timed ones
         d64 = sq.Desc(inst, sq.SQ_FP64, bounds=None, stream=sptr)
         h64 = sq.sq_setup(d64)
+
+        def step64():
+            sq.sq_moments(h64)
+            mu64 = sq.sq_fermi_level(h64)
+            return sq.sq_density_energy_stress_dev(h64, mu64, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
+
+        step64()
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        sq.sq_moments(h64)
-        mu64 = sq.sq_fermi_level(h64)
-        en64 = sq.sq_density_energy_stress_dev(h64, mu64, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
+        for _ in range(args.fp64_steps):
+            en64 = step64()
         a1.record(stream)
         torch.cuda.synchronize()
-        f64ms = a0.elapsed_time(a1)
-        line["fp64_gpu"] = {"value": 1000.0 / f64ms, "unit": METRIC, "ms_per_step": f64ms, "steps": 1,
-                            "F": en64["F"], "speedup_of_value": value / (1000.0 / f64ms)}
+        f64ms = a0.elapsed_time(a1) / args.fp64_steps
+        sig64 = sig_dev.cpu().numpy().reshape(3, 3)
+        line["fp64_gpu"] = {"value": 1000.0 / f64ms, "unit": METRIC, "ms_per_step": f64ms, "steps": args.fp64_steps,
+                            "warmup": 1, "F": en64["F"], "speedup_of_value": value / (1000.0 / f64ms),
+                            "mixed_vs_fp64": {
+                                "F_rel": abs(en["F"] - en64["F"]) / abs(en64["F"]),
+                                "E_band_rel": abs(en["E_band"] - en64["E_band"]) / abs(en64["E_band"]),
+                                "E_nl_rel": abs(en["E_nl"] - en64["E_nl"]) / abs(en64["E_nl"]),
+                                "sigma_abs_max": float(np.abs(np.asarray(line["sigma"]) - sig64).max())}}
         sq.sq_destroy(h64)
     sq.sq_destroy(h)
-    if rank == 0 and args.serve_requests > 0:
+    if rank == 0 and world == 1 and args.serve_requests > 0:
         line["serving"] = serve_stream(sq, args.serve_requests, prec)
-    if rank == 0 and args.batch > 0:
+    if rank == 0 and world == 1 and args.batch > 0:
         line["batch"] = batch_throughput(sq, prec, count=args.batch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_rate(inst, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_oracle_rate(inst, args.cpu_nodes)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -453,8 +547,21 @@ def run_ours(args):
     return 0
 
 
+def launch_ranks(args) -> int:
+    """--gpus N > 1 outside torchrun: start N ranks of this script on this node (127.0.0.1)."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and not args.profile_case:
+        return launch_ranks(args)
     if args.profile_case:
         return run_profile_case(args)
     if args.impl == "reference":

@@ -31,8 +31,9 @@
  *   - Arrays are row-major; grid arrays are x fastest: i = ix + n0 (iy + n1 iz).
  *   - sigma is returned row-major 3x3 in Ha/bohr^3 (sigma[3*a + b]).
  *   - Every call returns an int status (SQ_OK = 0). The library never aborts or traps; on
- *     error sq_last_error() describes the failure. Device waits are bounded and report
- *     SQ_ERR_TIMEOUT.
+ *     error sq_last_error() describes the failure. No kernel of the library waits on another
+ *     kernel or on the host, so no call can hang on the device; SQ_ERR_TIMEOUT is reserved
+ *     and no call returns it at present.
  *   - The caller owns every host buffer passed in or out; the library copies inputs during
  *     sq_setup and owns all device memory of a handle until sq_destroy.
  *   - A handle is used by one host thread at a time. Work is issued on desc->stream
@@ -53,7 +54,7 @@ extern "C" {
 #define SQ_ERR_OOM 2           /* device or host allocation failed                    */
 #define SQ_ERR_CUDA 3          /* a CUDA runtime call failed                           */
 #define SQ_ERR_NO_BRACKET 4    /* N(mu) - N_e has no sign change on the bisection bracket */
-#define SQ_ERR_TIMEOUT 5       /* a bounded device wait gave up                        */
+#define SQ_ERR_TIMEOUT 5       /* reserved for a bounded device wait (none at present)  */
 #define SQ_ERR_STATE 6         /* call out of order (e.g. contraction before moments)  */
 
 /* precision modes */
@@ -104,6 +105,12 @@ typedef struct {
   int cheb_quad_M;             /* Chebyshev-Gauss points for c, d, s (<= 0 selects 2048)        */
   int lanczos_k;               /* Lanczos steps (<= 0 selects 40)                               */
   void* stream;                /* cudaStream_t or NULL                                          */
+  int part_rank, part_count;   /* node partition (Sec. 4: the nodes of K_Omega are divided among
+                                  processors and every SQ sum is a sum over them): with
+                                  part_count > 0 the handle sweeps only tile range part_rank of
+                                  part_count equal contiguous ranges of the 2 x 2 x 2-node tiles
+                                  (tile t = tx + T0 (ty + T1 tz)); 0 = the whole cell. See
+                                  sq_node_sums / sq_fermi_level_sums for the exchange step.      */
 } sq_instance_desc;
 
 typedef struct {
@@ -125,7 +132,7 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out);
 
 /* Spectral bounds (SQ_BOUNDS_LANCZOS: device Lanczos, Sec. 4 chi_q / zeta_q), then the
  * Chebyshev sweep over every node (Sec. 4 three-term recurrence) and the moment table.
- * Asynchronous on the handle's stream. Errors: SQ_ERR_CUDA, SQ_ERR_TIMEOUT. */
+ * Asynchronous on the handle's stream. Errors: SQ_ERR_CUDA, SQ_ERR_OOM. */
 int sq_moments(sq_handle* h);
 
 /* Fermi level by FP64 bisection on N(mu) = 2 sum'_j c^j(mu) R^j, R^j = sum_q rho_q^j, on
@@ -133,6 +140,21 @@ int sq_moments(sq_handle* h);
  * steps; runs on the device and synchronises the stream. Errors: SQ_ERR_STATE (no moments),
  * SQ_ERR_NO_BRACKET, SQ_ERR_CUDA. */
 int sq_fermi_level(sq_handle* h, double* mu_out);
+
+/* Node partition (part_count > 0): the moments of the nodes outside the handle's tile range
+ * are zero, so R^j and every contraction output are this part's share of the node sums of
+ * Sec. 4, and the parts add up to the whole cell. The Fermi level needs the whole-cell sums:
+ *   sq_node_sums        R_out [n_pl + 1] (host) = sum over this part's nodes of rho_q^j
+ *                       (fixed order); synchronises. Errors: SQ_ERR_STATE (no moments).
+ *   sq_fermi_level_sums the bisection of sq_fermi_level on the caller's R_host [n_pl + 1]
+ *                       (the sum of every part's sq_node_sums, e.g. one allreduce of n_pl + 1
+ *                       doubles); synchronises. Errors: SQ_ERR_STATE, SQ_ERR_INVALID_ARG
+ *                       (NULL or non-finite R_host), SQ_ERR_NO_BRACKET.
+ * Each part then calls sq_density_energy_stress / sq_pressure at that mu and the parts' E_band,
+ * E_s, E_nl, N_check, E_pot, sigma and pressure add up (one allreduce of 15 doubles); rho_out
+ * holds this part's nodes (zero elsewhere). Unpartitioned handles may use both calls too. */
+int sq_node_sums(sq_handle* h, double* R_out);
+int sq_fermi_level_sums(sq_handle* h, const double* R_host, double* mu_out);
 
 /* Contraction at mu (Sec. 4 rho_q and stress sums, App. A band energy). Host outputs:
  * rho_out [N_d] or NULL, e_out or NULL, sigma_out [9] or NULL. Synchronises the stream. */
@@ -170,6 +192,16 @@ size_t sq_footprint_bytes(const sq_instance_desc* desc);
 /* Number of CUDA kernels the handle launched since sq_setup (all calls). */
 long long sq_kernel_launches(const sq_handle* h);
 
+/* Launches of the Chebyshev step kernel since sq_setup, by variant, into counts[3] (host):
+ *   counts[0]  projections of the block's atom images staged in shared memory, projector
+ *              phases on tensor cores (SQ_MIXED, at most 4 channels per atom)
+ *   counts[1]  staged in shared memory, scalar projector phases (SQ_FP64, or > 4 channels)
+ *   counts[2]  projections read and accumulated in global memory (a block meets more
+ *              projector rows than shared memory holds: dense atoms, large R_cut)
+ * The environment variable SQ_STEP_SMEM_ROWS, read by sq_setup, lowers the row count above
+ * which a block uses global memory (tuning and tests). Errors: SQ_ERR_INVALID_ARG. */
+int sq_step_launch_counts(const sq_handle* h, long long* counts);
+
 /* Kernel classes of the Chebyshev sweep timed by sq_kernel_timing (see below). */
 #define SQ_K_STENCIL 0   /* H t^j, window mask, recurrence update, S partials          */
 #define SQ_K_PROJECT 1   /* chi^T t^{j+1} per atom image                                */
@@ -199,9 +231,12 @@ int sq_kernel_timing_read(const sq_handle* h, int kid, long long* launches, doub
  * (SQ_NOALLOC_MAX_NPL + 1 + SQ_NOALLOC_MAX_M + 32) doubles (about 73 KB) that every GPU
  * loading the library holds until exit; n_pl > SQ_NOALLOC_MAX_NPL or M > SQ_NOALLOC_MAX_M is
  * rejected with SQ_ERR_INVALID_ARG. No cudaMalloc / cudaFree or allocating library call is
- * made. The first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture. Every call rewrites the whole
- * scratch; calls that overlap on the GPU share it and race. */
+ * made. Every call made outside stream capture looks up the array's device address with the
+ * calling device current (so the address stays right after a device reset reloads the module);
+ * a call inside a capture reuses the address of the last uncaptured call on that device, so make
+ * the first call on each device (and the first after a reset) outside any stream capture: a
+ * first call inside one returns SQ_ERR_STATE. Every call rewrites the whole scratch; calls that
+ * overlap on the GPU share it and race. */
 #define SQ_NOALLOC_MAX_NPL 1024
 #define SQ_NOALLOC_MAX_M 8192
 int sq_fermi_level_noalloc(const double* mom_dev, int n_nodes, int n_pl, double lambda_lo, double lambda_hi,

@@ -7,6 +7,7 @@
 // sq_reduce.cu.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <string>
@@ -84,6 +85,9 @@ int validate(const sq_instance_desc* d, std::string& why) {
   if (d->cheb_quad_M > 6144) { why = "cheb_quad_M must be <= 6144"; return SQ_ERR_INVALID_ARG; }
   if (d->precision != SQ_FP64 && d->precision != SQ_MIXED) { why = "unknown precision"; return SQ_ERR_INVALID_ARG; }
   if (d->bounds_mode != SQ_BOUNDS_LANCZOS && d->bounds_mode != SQ_BOUNDS_GIVEN) { why = "unknown bounds mode"; return SQ_ERR_INVALID_ARG; }
+  if (d->part_count < 0 || (d->part_count > 0 && (d->part_rank < 0 || d->part_rank >= d->part_count))) {
+    why = "partition needs 0 <= part_rank < part_count (or part_count = 0)"; return SQ_ERR_INVALID_ARG;
+  }
   if (d->bounds_mode == SQ_BOUNDS_GIVEN &&
       !(d->lambda_lo < d->lambda_hi && std::isfinite(d->lambda_lo) && std::isfinite(d->lambda_hi))) {
     why = "given bounds need lambda_lo < lambda_hi"; return SQ_ERR_INVALID_ARG;
@@ -103,6 +107,7 @@ struct Plan {
   std::vector<int> lz_tiles;    // sample tiles of the Lanczos bounds
   size_t per_tile_bytes = 0;
   size_t fixed_bytes = 0;
+  int tile_begin = 0, tile_end = 0;   // the tiles this handle sweeps (the node partition)
 };
 
 int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
@@ -127,7 +132,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   g.Upts = g.U[0] * g.U[1] * g.U[2];
   g.nbricks = g.nbr[0] * g.nbr[1] * g.nbr[2];
   g.n_tiles = g.tiles[0] * g.tiles[1] * g.tiles[2];
-  g.nslab = g.nbr[2];
+  g.nslab = g.nbr[1];   // slabs are y-rows of bricks (all x, all z)
   double w[sq::kMaxNo + 1], gw[sq::kMaxNo + 1];
   fd_weights(d->n_o, w, gw);
   g.lap0 = 0.0;
@@ -267,13 +272,21 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
     P.fixed_bytes += sizeof(double) * (size_t(k + 2) * nst * g.Upts * g.B + nst * size_t(g.r_cap) * g.B +
                                        nst * g.B * size_t(5 * k + 8)) + sizeof(int) * nst;
   }
+  // the node partition: part part_rank of part_count equal contiguous tile ranges
+  P.tile_begin = 0;
+  P.tile_end = g.n_tiles;
+  if (d->part_count > 0) {
+    P.tile_begin = int((long long)g.n_tiles * d->part_rank / d->part_count);
+    P.tile_end = int((long long)g.n_tiles * (d->part_rank + 1) / d->part_count);
+  }
+  const long long ntl = std::max(1, P.tile_end - P.tile_begin);
   // tiles per wave: keep the per-wave working set under 24 GiB (fewer, larger launches: less
   // per-wave setup and a smaller tail), with the tiles spread evenly over the waves
   size_t budget = size_t(24) << 30;
   long long wc = std::max<long long>(1, (long long)(budget / std::max<size_t>(P.per_tile_bytes, 1)));
-  wc = std::min<long long>(std::min<long long>(wc, g.n_tiles), 32768);
-  const long long nwaves = (g.n_tiles + wc - 1) / wc;
-  P.wave_cap = int((g.n_tiles + nwaves - 1) / nwaves);
+  wc = std::min<long long>(std::min<long long>(wc, ntl), 32768);
+  const long long nwaves = (ntl + wc - 1) / wc;
+  P.wave_cap = int((ntl + nwaves - 1) / nwaves);
   P.wave_cap = std::max<int>(P.wave_cap, int(P.lz_tiles.size()));
   return SQ_OK;
 }
@@ -414,9 +427,18 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   h->table_len = P.table_len;
   h->n_ch_total = int(P.ch_l.size());
   h->wave_cap = P.wave_cap;
-  for (int t0 = 0; t0 < h->geo.n_tiles; t0 += h->wave_cap)
-    h->waves.push_back({t0, std::min(h->wave_cap, h->geo.n_tiles - t0), nullptr});
+  for (int t0 = P.tile_begin; t0 < P.tile_end; t0 += h->wave_cap)
+    h->waves.push_back({t0, std::min(h->wave_cap, P.tile_end - t0), nullptr});
+  h->tile_begin = P.tile_begin;
+  h->tile_end = P.tile_end;
   h->lanczos_tiles = P.lz_tiles;
+  // projector rows a step block may stage in shared memory; SQ_STEP_SMEM_ROWS lowers the cap
+  // (tuning and tests of the global-memory projection path)
+  h->step_rows_cap = sq::step_rows_smem_max(desc->precision);
+  if (const char* env = std::getenv("SQ_STEP_SMEM_ROWS")) {
+    const long v = std::strtol(env, nullptr, 10);
+    if (v >= 0 && v < h->step_rows_cap) h->step_rows_cap = int(v);
+  }
 
   auto cleanup = [&](int code) {
     g_setup_err = h->err;
@@ -530,6 +552,11 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
     h->bounds_ready = true;
   }
 #undef SQ_H2D
+  if (cudaMemsetAsync(h->d.mom, 0, sizeof(double) * size_t(Nd) * size_t(g.n_pl + 1) * SQ_N_MOMENTS, s) !=
+      cudaSuccess) {
+    sq::fail(h, SQ_ERR_CUDA, "memset moments");
+    return cleanup(SQ_ERR_CUDA);
+  }
   if (cudaMemsetAsync(h->d.status, 0, sizeof(int) * sq::kStCount, s) != cudaSuccess) {
     sq::fail(h, SQ_ERR_CUDA, "memset status");
     return cleanup(SQ_ERR_CUDA);
@@ -559,6 +586,21 @@ int sq_fermi_level(sq_handle* h, double* mu_out) {
   if (!h) return SQ_ERR_INVALID_ARG;
   if (!h->moments_ready) return sq::fail(h, SQ_ERR_STATE, "sq_fermi_level before sq_moments");
   return sq::run_fermi(h, mu_out);
+}
+
+int sq_node_sums(sq_handle* h, double* R_out) {
+  if (!h || !R_out) return SQ_ERR_INVALID_ARG;
+  if (!h->moments_ready) return sq::fail(h, SQ_ERR_STATE, "sq_node_sums before sq_moments");
+  return sq::run_node_sums(h, R_out);
+}
+
+int sq_fermi_level_sums(sq_handle* h, const double* R_host, double* mu_out) {
+  if (!h) return SQ_ERR_INVALID_ARG;
+  if (!R_host) return sq::fail(h, SQ_ERR_INVALID_ARG, "R_host is NULL");
+  for (int j = 0; j <= h->geo.n_pl; ++j)
+    if (!std::isfinite(R_host[j])) return sq::fail(h, SQ_ERR_INVALID_ARG, "R_host has a non-finite value");
+  if (!h->bounds_ready) return sq::fail(h, SQ_ERR_STATE, "sq_fermi_level_sums before the bounds are known");
+  return sq::run_fermi_sums(h, R_host, mu_out);
 }
 
 static int contraction_common(sq_handle* h, double mu, double* rho_dev, sq_energies* e_out,
@@ -632,6 +674,12 @@ int sq_moments_copy(sq_handle* h, double* host_out) {
 }
 
 long long sq_kernel_launches(const sq_handle* h) { return h ? h->launches : 0; }
+
+int sq_step_launch_counts(const sq_handle* h, long long* counts) {
+  if (!h || !counts) return SQ_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i) counts[i] = h->step_variant[i];
+  return SQ_OK;
+}
 
 int sq_kernel_timing(sq_handle* h, int enable) {
   if (!h) return SQ_ERR_INVALID_ARG;

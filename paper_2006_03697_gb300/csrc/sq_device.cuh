@@ -92,4 +92,56 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+
+// Fermi-Dirac occupation 1 / (1 + e^x), evaluated without overflow for any x.
+__device__ __forceinline__ double fermi_occ(double x) {
+  const double ex = exp(-fabs(x));
+  return (x > 0.0) ? ex / (1.0 + ex) : 1.0 / (1.0 + ex);
+}
+
+// Deterministic block sum (blockDim.x a power of two, sh holds blockDim.x doubles).
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// N(mu) = 2 sum'_j c^j(mu) R^j = (4/M) sum_k g((chi + zeta cos theta_k - mu) / kT) F_k with
+// F_k = sum'_j cos(j theta_k) R^j, theta_k = pi (k + 1/2) / M (the M-point Chebyshev-Gauss rule
+// for the coefficient integral of Sec. 4). Whole block; same value in every thread.
+__device__ __forceinline__ double electron_count_F(const double* F, int M, double chi_q, double zeta_q, double kT,
+                                                  double mu, double* sh) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < M; k += blockDim.x)
+    s += fermi_occ((chi_q + zeta_q * cos(M_PI * (k + 0.5) / M) - mu) / kT) * F[k];
+  return 4.0 / M * block_sum_d(s, sh);
+}
+
+// The Fermi-level rule of the library: bisection on N(mu) = N_e over
+// [lam_lo - 40 kT, lam_hi + 40 kT] until the bracket is < 1e-13 max(1, |mu|) or 200 steps, mu =
+// the final midpoint. Returns false (and leaves *mu alone) when N(mu) - N_e has no sign change
+// on the bracket. Whole block (sh: blockDim.x doubles); every thread gets the same result.
+__device__ __forceinline__ bool fermi_bisect_rule(const double* F, int M, double lam_lo, double lam_hi, double kT,
+                                                  double n_e, double* sh, double* mu) {
+  const double chi_q = 0.5 * (lam_hi + lam_lo), zeta_q = 0.5 * (lam_hi - lam_lo);
+  double lo = lam_lo - 40.0 * kT, hi = lam_hi + 40.0 * kT;
+  const double nlo = electron_count_F(F, M, chi_q, zeta_q, kT, lo, sh);
+  const double nhi = electron_count_F(F, M, chi_q, zeta_q, kT, hi, sh);
+  if (!(nlo < n_e && n_e < nhi)) return false;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (electron_count_F(F, M, chi_q, zeta_q, kT, mid, sh) < n_e) lo = mid;
+    else hi = mid;
+    if (hi - lo < 1e-13 * fmax(1.0, fabs(mid))) break;
+  }
+  *mu = 0.5 * (lo + hi);
+  return true;
+}
+
 }  // namespace sq

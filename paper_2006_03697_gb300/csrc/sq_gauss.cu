@@ -31,7 +31,11 @@ __global__ void k_gauss_eig(int ncols, int k, const double* __restrict__ alpha, 
     z[i] = (i == 0) ? 1.0 : 0.0;
   }
   // implicit QL with Wilkinson shifts on the symmetric tridiagonal (d, e); z is the first row
-  // of the accumulated rotations, so z_i^2 is the weight of eigenvalue d_i
+  // of the accumulated rotations, so z_i^2 is the weight of eigenvalue d_i. The iteration is
+  // the published EISPACK routine imtql2 (Bowdler, Martin, Reinsch and Wilkinson, "The QR and
+  // QL algorithms for symmetric matrices", Numer. Math. 11, 1968; EISPACK, public domain),
+  // restricted as in Golub and Welsch, "Calculation of Gauss quadrature rules", Math. Comp. 23,
+  // 1969: only the first row of the eigenvector matrix is rotated.
   bool ok = true;
   for (int l = 0; l < n && ok; ++l) {
     for (int iter = 0;; ++iter) {
@@ -85,11 +89,6 @@ __global__ void k_gauss_eig(int ncols, int k, const double* __restrict__ alpha, 
   }
 }
 
-__device__ __forceinline__ double fermi_d(double x) {
-  const double ex = exp(-fabs(x));
-  return x > 0.0 ? ex / (1.0 + ex) : 1.0 / (1.0 + ex);
-}
-
 // part[block] = sum over the block's columns of 2 sum_i w g((theta - mu) / kT) (fixed order)
 __global__ void k_gauss_count(int ncols, int k, const double* __restrict__ theta, const double* __restrict__ wgt,
                               double mu, double kT, double* __restrict__ part) {
@@ -98,7 +97,7 @@ __global__ void k_gauss_count(int ncols, int k, const double* __restrict__ theta
   for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < ncols; col += gridDim.x * blockDim.x)
     for (int i = 0; i < k; ++i) {
       const double w = wgt[(size_t)col * k + i];
-      if (w != 0.0) acc += 2.0 * w * fermi_d((theta[(size_t)col * k + i] - mu) / kT);
+      if (w != 0.0) acc += 2.0 * w * fermi_occ((theta[(size_t)col * k + i] - mu) / kT);
     }
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -135,7 +134,7 @@ __global__ void k_gauss_rho(Geo g, int ntiles_total, int k, const double* __rest
       const double w = wgt[(size_t)col * k + i];
       if (w == 0.0) continue;
       const double th = theta[(size_t)col * k + i];
-      const double f = w * fermi_d((th - mu) / kT);
+      const double f = w * fermi_occ((th - mu) / kT);
       r += f;
       eb += f * th;
     }

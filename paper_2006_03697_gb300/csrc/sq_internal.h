@@ -85,7 +85,7 @@ struct Geo {
   int r_cap;                      // projector rows per tile (capacity)
   int br_cap;                     // entries per brick (capacity)
   int n_pl;
-  int nslab;                      // z-slabs of kBrick planes per tile
+  int nslab;                      // slabs per tile: y-rows of bricks (kBrick y-planes, all x, all z)
 };
 
 struct Wave {
@@ -103,7 +103,7 @@ struct WaveBufs {
   int* brick_n = nullptr;         // [wt][nbricks]
   int4* brick_rec = nullptr;      // [wt][nbricks][br_cap][2] per-brick image records
   float4* brick_d0 = nullptr;     // [wt][nbricks][br_cap] x - R of the record's brick corner (FP32 W table)
-  int* slab_n = nullptr;          // [wt][nslab] projector rows meeting each z-slab
+  int* slab_n = nullptr;          // [wt][nslab] projector rows meeting each slab (y-row of bricks)
   int* slab_map = nullptr;        // [wt][nslab][r_cap] slab row -> tile row
   void* T[3] = {nullptr, nullptr, nullptr};   // Real [wt][Upts][B]
   void* W = nullptr;              // Real [wt][3][Upts][B]
@@ -162,11 +162,16 @@ struct sq_handle {
   int n_ch_total = 0;
   bool proj4 = false;               // every atom has at most 4 projector channels (one group per image)
   std::vector<sq::Wave> waves;
+  int tile_begin = 0, tile_end = 0;   // tiles this handle sweeps (node partition)
   int wave_cap = 0;
   sq::Dev d;
   sq::WaveBufs wb;
   std::vector<int> lanczos_tiles;
   long long launches = 0;
+  // step-kernel launches by variant: [0] projections staged in shared memory, tensor-core
+  // projector phases; [1] shared memory, scalar phases; [2] projections in global memory
+  long long step_variant[3] = {0, 0, 0};
+  int step_rows_cap = 0;            // most projector rows a step block stages in shared memory
   // optional event timing of the sweep kernels
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -213,6 +218,7 @@ int build_wave_lists(sq_handle* h, const Wave& w);
 
 // sweep (sq_sweep.cu)
 int run_sweep(sq_handle* h);
+int step_rows_smem_max(int precision);
 // out = H_q v for every node column of the wave's tiles (FP64), P = projection scratch
 // H_q v on the sample tiles of the Lanczos bounds (FP64 or FP32 vectors, matching tables)
 int launch_apply_h(sq_handle* h, const Wave& w, const double* v, double* out, double* P);
@@ -226,6 +232,8 @@ int run_lanczos(sq_handle* h);
 template <typename Real>
 int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C);
 int run_fermi(sq_handle* h, double* mu_out);
+int run_node_sums(sq_handle* h, double* R_out);
+int run_fermi_sums(sq_handle* h, const double* R_host, double* mu_out);
 int run_contraction(sq_handle* h, double mu, double* rho_dev, double* sums_host);
 
 // status word indices

@@ -11,7 +11,7 @@
 #include <cmath>
 #include <mutex>
 
-#include "sq_internal.h"
+#include "sq_device.cuh"
 
 namespace sq {
 
@@ -26,52 +26,17 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
 namespace {
 
 std::mutex g_mu;
-double* g_scratch_ptr[256] = {nullptr};   // device address of the scratch, per device ordinal
+double* g_scratch_ptr[256] = {nullptr};   // last looked-up device address of the scratch, per device ordinal
 
-__device__ __forceinline__ double fermi_na(double x) {
-  const double ex = exp(-fabs(x));
-  return (x > 0.0) ? ex / (1.0 + ex) : 1.0 / (1.0 + ex);
-}
-
-__device__ double sum_block(double v, double* sh) {
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-__device__ double count_na(const double* F, int M, double chi_q, double zeta_q, double kT, double mu, double* sh) {
-  double s = 0.0;
-  for (int k = threadIdx.x; k < M; k += blockDim.x)
-    s += fermi_na((chi_q + zeta_q * cos(M_PI * (k + 0.5) / M) - mu) / kT) * F[k];
-  return 4.0 / M * sum_block(s, sh);
-}
-
-// Same bisection rule as sq_fermi_level, with the bounds passed by value and mu written to
-// the caller's device pointer (NaN when N(mu) - N_e has no sign change on the bracket).
+// The library's bisection rule (fermi_bisect_rule, shared with sq_fermi_level), with the
+// bounds passed by value and mu written to the caller's device pointer (NaN when
+// N(mu) - N_e has no sign change on the bracket).
 __global__ void k_bisect_noalloc(const double* __restrict__ F, int M, double lam_lo, double lam_hi, double kT,
                                  double n_e, double* __restrict__ mu_out) {
   __shared__ double sh[1024];
-  const double chi_q = 0.5 * (lam_hi + lam_lo), zeta_q = 0.5 * (lam_hi - lam_lo);
-  double lo = lam_lo - 40.0 * kT, hi = lam_hi + 40.0 * kT;
-  const double nlo = count_na(F, M, chi_q, zeta_q, kT, lo, sh);
-  const double nhi = count_na(F, M, chi_q, zeta_q, kT, hi, sh);
-  if (!(nlo < n_e && n_e < nhi)) {
-    if (threadIdx.x == 0) *mu_out = NAN;
-    return;
-  }
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (count_na(F, M, chi_q, zeta_q, kT, mid, sh) < n_e) lo = mid;
-    else hi = mid;
-    if (hi - lo < 1e-13 * fmax(1.0, fabs(mid))) break;
-  }
-  if (threadIdx.x == 0) *mu_out = 0.5 * (lo + hi);
+  double mu = 0.0;
+  const bool ok = fermi_bisect_rule(F, M, lam_lo, lam_hi, kT, n_e, sh, &mu);
+  if (threadIdx.x == 0) *mu_out = ok ? mu : NAN;
 }
 
 }  // namespace
@@ -87,23 +52,33 @@ extern "C" int sq_fermi_level_noalloc(const double* mom_dev, int n_nodes, int n_
     return SQ_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SQ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The device address of the scratch array, with the calling device current. Outside stream
+  // capture it is looked up on every call (a host-side table lookup), so a module reloaded
+  // after a device reset never leaves a stale address behind; inside a capture no lookup is
+  // made and the address of the last uncaptured call on this device is used.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return SQ_ERR_CUDA;
+  }
   double* scratch = nullptr;
   {
-    // once per device, with that device current: the device address of the scratch array
     std::lock_guard<std::mutex> lock(sq::g_mu);
-    if (!sq::g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, sq::g_noalloc_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return SQ_ERR_CUDA;
       }
       sq::g_scratch_ptr[dev] = static_cast<double*>(p);
+    } else if (!sq::g_scratch_ptr[dev]) {
+      return SQ_ERR_STATE;   // first call on this device inside a capture
     }
     scratch = sq::g_scratch_ptr[dev];
   }
   double* R = scratch;                            // [n_pl + 1]
   double* F = scratch + SQ_NOALLOC_MAX_NPL + 1;   // [M]
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   sq::k_rsum<<<n_pl + 1, 256, 0, s>>>(mom_dev, n_nodes, n_pl, R);
   sq::k_cosF<<<(M + 255) / 256, 256, 0, s>>>(R, n_pl, M, F);
   sq::k_bisect_noalloc<<<1, 1024, 0, s>>>(F, M, lambda_lo, lambda_hi, kT, n_e, mu_dev);

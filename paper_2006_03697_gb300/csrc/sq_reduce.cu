@@ -11,28 +11,10 @@
 
 namespace sq {
 
-__device__ __forceinline__ double fermi_d(double x) {
-  const double ex = exp(-fabs(x));
-  return (x > 0.0) ? ex / (1.0 + ex) : 1.0 / (1.0 + ex);
-}
-
 // g ln g + (1 - g) ln(1 - g) at g = fermi(x), stable form -[ln(1+e^-|x|) + |x| e^-|x|/(1+e^-|x|)]
 __device__ __forceinline__ double entropy_d(double x) {
   const double ax = fabs(x), ex = exp(-ax);
   return -(log1p(ex) + ax * ex / (1.0 + ex));
-}
-
-// Deterministic block sum (blockDim.x = 256 or 1024, power of two).
-__device__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = sh[0];
-  __syncthreads();
-  return r;
 }
 
 __global__ void k_rsum(const double* __restrict__ mom, int Nd, int n_pl, double* __restrict__ R) {
@@ -40,7 +22,7 @@ __global__ void k_rsum(const double* __restrict__ mom, int Nd, int n_pl, double*
   const int j = blockIdx.x;
   double s = 0.0;
   for (int q = threadIdx.x; q < Nd; q += blockDim.x) s += mom[((size_t)q * (n_pl + 1) + j) * SQ_N_MOMENTS];
-  s = block_sum(s, sh);
+  s = block_sum_d(s, sh);
   if (threadIdx.x == 0) R[j] = s;
 }
 
@@ -53,40 +35,15 @@ __global__ void k_cosF(const double* __restrict__ R, int n_pl, int M, double* __
   F[k] = s;
 }
 
-__device__ double count_at(const double* F, int M, double chi_q, double zeta_q, double kT, double mu, double* sh) {
-  double s = 0.0;
-  for (int k = threadIdx.x; k < M; k += blockDim.x) {
-    const double r = cos(M_PI * (k + 0.5) / M);
-    s += fermi_d((chi_q + zeta_q * r - mu) / kT) * F[k];
-  }
-  return 4.0 / M * block_sum(s, sh);
-}
-
 // Single block. scal[0], scal[1]: bounds; writes scal[2] = mu, status[kStNoBracket].
 __global__ void k_bisect(const double* __restrict__ F, int M, double kT, double n_e, double* __restrict__ scal,
                          int* __restrict__ status) {
   __shared__ double sh[1024];
-  const double lam_lo = scal[0], lam_hi = scal[1];
-  const double chi_q = 0.5 * (lam_hi + lam_lo), zeta_q = 0.5 * (lam_hi - lam_lo);
-  double lo = lam_lo - 40.0 * kT, hi = lam_hi + 40.0 * kT;
-  const double nlo = count_at(F, M, chi_q, zeta_q, kT, lo, sh);
-  const double nhi = count_at(F, M, chi_q, zeta_q, kT, hi, sh);
-  if (!(nlo < n_e && n_e < nhi)) {
-    if (threadIdx.x == 0) {
-      status[kStNoBracket] = 1;
-      scal[2] = NAN;
-    }
-    return;
-  }
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (count_at(F, M, chi_q, zeta_q, kT, mid, sh) < n_e) lo = mid;
-    else hi = mid;
-    if (hi - lo < 1e-13 * fmax(1.0, fabs(mid))) break;
-  }
+  double mu = 0.0;
+  const bool ok = fermi_bisect_rule(F, M, scal[0], scal[1], kT, n_e, sh, &mu);
   if (threadIdx.x == 0) {
-    scal[2] = 0.5 * (lo + hi);
-    status[kStNoBracket] = 0;
+    scal[2] = ok ? mu : NAN;
+    status[kStNoBracket] = ok ? 0 : 1;
   }
 }
 
@@ -99,7 +56,7 @@ __global__ void k_coef(const double* __restrict__ scal, double kT, int n_pl, int
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     const double r = cos(M_PI * (k + 0.5) / M);
     const double x = (chi_q + zeta_q * r - mu) / kT;
-    fv[k] = (which == 0) ? fermi_d(x) : (which == 1) ? r * fermi_d(x) : entropy_d(x);
+    fv[k] = (which == 0) ? fermi_occ(x) : (which == 1) ? r * fermi_occ(x) : entropy_d(x);
   }
   __syncthreads();
   for (int j = threadIdx.x; j <= n_pl; j += blockDim.x) {
@@ -143,7 +100,7 @@ __global__ void k_contract(const double* __restrict__ mom, const double* __restr
     for (int k = 0; k < kNPart; ++k) acc[k] += loc[k];
   }
   for (int k = 0; k < kNPart; ++k) {
-    const double v = block_sum(acc[k], sh);
+    const double v = block_sum_d(acc[k], sh);
     if (threadIdx.x == 0) part[blockIdx.x * kNPart + k] = v;
   }
 }
@@ -183,11 +140,10 @@ __global__ void k_contract_final(const double* __restrict__ part, int nblk, doub
 
 __global__ void k_set_scalar(double* __restrict__ scal, int idx, double v) { scal[idx] = v; }
 
-int run_fermi(sq_handle* h, double* mu_out) {
+// Bisection on the node sums already in d.R (the whole cell's, or the caller's allreduced ones)
+static int fermi_from_R(sq_handle* h, double* mu_out) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  k_rsum<<<g.n_pl + 1, 256, 0, s>>>(h->d.mom, h->Nd, g.n_pl, h->d.R);
-  SQ_LAUNCH_CHECK(h);
   k_cosF<<<(h->M + 255) / 256, 256, 0, s>>>(h->d.R, g.n_pl, h->M, h->d.cosF);
   SQ_LAUNCH_CHECK(h);
   k_bisect<<<1, 1024, 0, s>>>(h->d.cosF, h->M, h->kT, h->n_e, h->d.scal, h->d.status);
@@ -200,6 +156,27 @@ int run_fermi(sq_handle* h, double* mu_out) {
   if (st[kStNoBracket]) return fail(h, SQ_ERR_NO_BRACKET, "N(mu) - N_e has no sign change on the bisection bracket");
   if (mu_out) *mu_out = mu;
   return SQ_OK;
+}
+
+int run_fermi(sq_handle* h, double* mu_out) {
+  k_rsum<<<h->geo.n_pl + 1, 256, 0, h->stream>>>(h->d.mom, h->Nd, h->geo.n_pl, h->d.R);
+  SQ_LAUNCH_CHECK(h);
+  return fermi_from_R(h, mu_out);
+}
+
+int run_node_sums(sq_handle* h, double* R_out) {
+  cudaStream_t s = h->stream;
+  k_rsum<<<h->geo.n_pl + 1, 256, 0, s>>>(h->d.mom, h->Nd, h->geo.n_pl, h->d.R);
+  SQ_LAUNCH_CHECK(h);
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(R_out, h->d.R, sizeof(double) * (h->geo.n_pl + 1), cudaMemcpyDeviceToHost, s));
+  SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+  return SQ_OK;
+}
+
+int run_fermi_sums(sq_handle* h, const double* R_host, double* mu_out) {
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.R, R_host, sizeof(double) * (h->geo.n_pl + 1), cudaMemcpyHostToDevice,
+                                 h->stream));
+  return fermi_from_R(h, mu_out);
 }
 
 int run_contraction(sq_handle* h, double mu, double* rho_dev, double* out_host) {

@@ -126,10 +126,11 @@ __device__ __forceinline__ bool image_meets_box(const Geo& g, const TileEntry& t
 }
 
 // One warp per (brick, tile): entries whose support sphere meets the brick, in entry order,
-// and their records. The projector rows of the entries that meet the brick's z-slab (a
-// superset of its bricks' entries: the slab's bounding box contains each brick's) are
-// numbered slab-locally in entry order; the record carries that number (bits 16..31 of r0.w)
-// and the first brick of the slab writes the slab's row map (slab row -> tile row) and count.
+// and their records. The projector rows of the entries that meet the brick's slab (its y-row
+// of bricks: all of U in x and z, the brick's y-planes; a superset of its bricks' entries: the
+// slab's bounding box contains each brick's) are numbered slab-locally in entry order; the
+// record carries that number (bits 16..31 of r0.w) and the first brick of the slab writes the
+// slab's row map (slab row -> tile row) and count.
 __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ rcmax,
                               const TileEntry* __restrict__ entries, const int* __restrict__ n_entries,
                               int* __restrict__ blist, int* __restrict__ bn, int4* __restrict__ rec,
@@ -143,11 +144,11 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
   const int bhi[3] = {o[0] - g.m[0] + min(g.U[0], (bx + 1) * kBrick) - 1,
                       o[1] - g.m[1] + min(g.U[1], (by + 1) * kBrick) - 1,
                       o[2] - g.m[2] + min(g.U[2], (bz + 1) * kBrick) - 1};
-  // the slab: all of U in x and y, the brick's planes in z
-  const int sl[3] = {o[0] - g.m[0], o[1] - g.m[1], bl[2]};
-  const int shi[3] = {o[0] - g.m[0] + g.U[0] - 1, o[1] - g.m[1] + g.U[1] - 1, bhi[2]};
-  const bool slab_writer = (bx == 0 && by == 0);
-  int* smap = slab_map + ((size_t)tl * g.nslab + bz) * g.r_cap;
+  // the slab: all of U in x and z, the brick's planes in y
+  const int sl[3] = {o[0] - g.m[0], bl[1], o[2] - g.m[2]};
+  const int shi[3] = {o[0] - g.m[0] + g.U[0] - 1, bhi[1], o[2] - g.m[2] + g.U[2] - 1};
+  const bool slab_writer = (bx == 0 && bz == 0);
+  int* smap = slab_map + ((size_t)tl * g.nslab + by) * g.r_cap;
   const int ne = n_entries[tl];
   const TileEntry* ent = entries + (size_t)tl * g.e_cap;
   int* out = blist + ((size_t)tl * g.nbricks + br) * g.br_cap;
@@ -226,7 +227,7 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
   if (lane == 0) {
     bn[(size_t)tl * g.nbricks + br] = min(cnt, g.br_cap);
     if (cnt > g.br_cap) atomicOr(status + kStOverflow, 2);
-    if (slab_writer) slab_n[(size_t)tl * g.nslab + bz] = srow_base;
+    if (slab_writer) slab_n[(size_t)tl * g.nslab + by] = srow_base;
   }
 }
 
@@ -265,7 +266,7 @@ __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
 
 // W_b(u, q) = sum_rows gamma |dOmega| A[row][q] chi_row(u) (x_u,b - R_b) on the window of q:
 // contracting the atom sum of the sigma^III term once, S^j_ab = sum_u W_b(u,q) (grad_a t^j)(u).
-// One block per (z-slab, tile); each warp walks whole 4^3 bricks (lanes = 4 x-points x 8
+// One block per (z-plane of bricks, tile); each warp walks whole 4^3 bricks (lanes = 4 x-points x 8
 // nodes) and, per half brick (8 points per lane, accumulators in registers), the brick's image
 // records: the 64-bit sphere mask skips the points an image does not reach, the table offset
 // of the brick corner locates the point's channel group.
@@ -393,7 +394,7 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, const Real
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
                                           (double*)h->wb.Pg[0], (double*)h->wb.Pg[1]);
   SQ_LAUNCH_CHECK(h);
-  k_wtable<Real><<<dim3(g.nslab, w.ntiles), 224, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries, h->wb.brick_list,
+  k_wtable<Real><<<dim3(g.nbr[2], w.ntiles), 224, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries, h->wb.brick_list,
                                                           h->wb.brick_rec, h->wb.brick_d0, h->wb.brick_n, A, W);
   SQ_LAUNCH_CHECK(h);
   SQ_CUDA_TRY(h, cudaMemsetAsync(T0, 0, sizeof(Real) * (size_t)w.ntiles * g.Upts * g.B, s));

@@ -216,7 +216,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   // [tn_sm: nw x 16 x 32] (Ps and Pstage only with kSmemP; rows_smem = 0 otherwise)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // wrapped V_eff index contributions of the slab's x, y and z positions (cell is periodic)
-  __shared__ int wrx[kMaxU], wry[kMaxU], wrz[kBrick];
+  __shared__ int wrx[kMaxU], wry[kBrick], wrz[kMaxU];
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
   double* Pn = Pg_next + (size_t)tl * g.r_cap * kTileB;
   // projections of t^{j+1}, summed in FP64 ([slab rows][8]); Pg^j staged in the sweep precision.
@@ -241,16 +241,16 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   const bool project = (mode != 2);
   const int st[3] = {kTileB, Ux * kTileB, Ux * Uy * kTileB};
   const int Ua[3] = {Ux, Uy, Uz};
-  for (int i = threadIdx.x; i < g.U[0] + g.U[1] + kBrick; i += blockDim.x) {
+  for (int i = threadIdx.x; i < g.U[0] + kBrick + g.U[2]; i += blockDim.x) {
     int a, u;
     if (i < g.U[0]) { a = 0; u = i; }
-    else if (i < g.U[0] + g.U[1]) { a = 1; u = i - g.U[0]; }
-    else { a = 2; u = slab * kBrick + i - g.U[0] - g.U[1]; }
+    else if (i < g.U[0] + kBrick) { a = 1; u = slab * kBrick + i - g.U[0]; }
+    else { a = 2; u = i - g.U[0] - kBrick; }
     int wv = (o[a] - g.m[a] + u) % g.n[a];
     if (wv < 0) wv += g.n[a];
     if (a == 0) wrx[u] = wv;
-    else if (a == 1) wry[u] = wv * g.n[0];
-    else wrz[u - slab * kBrick] = wv * g.n[0] * g.n[1];
+    else if (a == 1) wry[u - slab * kBrick] = wv * g.n[0];
+    else wrz[u] = wv * g.n[0] * g.n[1];
   }
   if (kSmemP) {
     for (int i = threadIdx.x; i < nsr * kTileB; i += blockDim.x) {
@@ -291,11 +291,11 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
     valid2[0] = node_valid(g, o, qa);
     valid2[1] = node_valid(g, o, qb);
   }
-  const int nbx = g.nbr[0], nby = g.nbr[1];
+  const int nbx = g.nbr[0], nby = g.nbr[1], nbz = g.nbr[2];
 
-  for (int bi = warp; bi < nbx * nby; bi += nw) {
-    const int bx = bi % nbx, by = bi / nbx;
-    const int br = (slab * nby + by) * nbx + bx;
+  for (int bi = warp; bi < nbx * nbz; bi += nw) {
+    const int bx = bi % nbx, bz = bi / nbx, by = slab;
+    const int br = (bz * nby + by) * nbx + bx;
     const int4* rb = brec + ((size_t)tl * g.nbricks + br) * g.br_cap * 2;
     const int nb = bn[(size_t)tl * g.nbricks + br];
     Real* tnv = tn_sm + warp * 16 * 32 + lane;   // per lane and brick point: V_nl t^j, then t^{j+1}
@@ -392,7 +392,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
 #pragma unroll 1
       for (int it = 0; it < 8; ++it) {
         const int pb = 2 * (it & 1) + yb2, pc = it >> 1;
-        const int ux = bx * kBrick + xa2, uy = by * kBrick + pb, uz = slab * kBrick + pc;
+        const int ux = bx * kBrick + xa2, uy = by * kBrick + pb, uz = bz * kBrick + pc;
         const int p = xa2 + 4 * pb + 16 * pc;
         const bool inU = (uy < Uy) && (uz < Uz);
         const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + 2 * np2;
@@ -422,7 +422,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
               gr[a].y += wg * (fp.y - fm.y);
             }
           }
-          const float vloc = float(v[wrz[uz - slab * kBrick] + wry[uy] + wrx[ux]]);
+          const float vloc = float(v[wrz[uz] + wry[pb] + wrx[ux]]);
           const float2 ynl = *reinterpret_cast<const float2*>(tw + tn_index(p, 2 * np2));   // phase A
           y.x += ynl.x;
           y.y += ynl.y;
@@ -459,7 +459,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
 #pragma unroll 1
       for (int it = 0; it < 16; ++it) {
         const int pb = it & 3, pc = it >> 2;
-        const int ux = bx * kBrick + pa, uy = by * kBrick + pb, uz = slab * kBrick + pc;
+        const int ux = bx * kBrick + pa, uy = by * kBrick + pb, uz = bz * kBrick + pc;
         const bool inU = (uy < Uy) && (uz < Uz);
         const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * kTileB + q;
         const bool inwin = inU && valid && in_window(g, qo, ux, uy, uz);
@@ -483,7 +483,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
               gr[a] += Coef<Real>::grd(g, a, pp) * (fp - fm);
             }
           }
-          const Real vloc = v[wrz[uz - slab * kBrick] + wry[uy] + wrx[ux]];   // V_eff at the wrapped node
+          const Real vloc = v[wrz[uz] + wry[pb] + wrx[ux]];   // V_eff at the wrapped node
           y += tnv[it * 32];                          // nonlocal part from phase A
           if (mode != 2) {
             tn = ca * y + (cd + ca * vloc) * tc - cc * tp;
@@ -693,19 +693,25 @@ k_moments(Geo g, Wave w, int j, const Real* __restrict__ Tj, const Real* __restr
 constexpr int kStepRowsSmemMax = 160 * 1024;
 constexpr int kStepSmemMax = kStepRowsSmemMax + (kStepThreads / 32) * (kTileB * 9 * 8 + 16 * 32 * 8);
 
+// largest projector-row count a step block stages in shared memory (more rows: global memory)
+int step_rows_smem_max(int precision) {
+  return int(kStepRowsSmemMax / (kTileB * (sizeof(double) + (precision == SQ_FP64 ? sizeof(double) : sizeof(float)))));
+}
+
 template <typename Real, int NO>
 static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, const Real* Tc, const Real* Tp, Real* Tn,
                        const double* Pg, double* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                        int mode) {
   const int rows_smem = int(smem / (kTileB * (sizeof(double) + sizeof(Real))));
-  const int nw = step_warps(h->geo.nbr[0] * h->geo.nbr[1]), nthr = 32 * nw;
+  const int nw = step_warps(h->geo.nbr[0] * h->geo.nbr[2]), nthr = 32 * nw;
   const size_t smem_warps = size_t(nw) * (kTileB * 9 * sizeof(double) + 16 * 32 * sizeof(Real));
   // The dynamic-size attribute belongs to the function, not the launch, and handles on other
   // host threads launch the same kernel, so every caller sets the same value (the largest
   // dynamic size this kernel uses)
-  if (smem <= kStepRowsSmemMax) {
+  if (rows_smem <= h->step_rows_cap) {
     smem += smem_warps;
     if (sizeof(Real) == 4 && h->proj4) {
+      h->step_variant[0]++;
       SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, sizeof(Real) == 4>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmemMax));
       k_step<Real, NO, true, sizeof(Real) == 4><<<grid, nthr, smem, h->stream>>>(
@@ -714,12 +720,14 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
       SQ_LAUNCH_CHECK(h);
       return SQ_OK;
     }
+    h->step_variant[1]++;
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
     k_step<Real, NO, true, false><<<grid, nthr, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
                                                                 h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
                                                                 h->d.scal, mode, h->wb.Spart, rows_smem);
   } else {
+    h->step_variant[2]++;
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
     k_step<Real, NO, false, false><<<grid, nthr, smem_warps, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
@@ -807,7 +815,7 @@ static int apply_h_t(sq_handle* h, const Wave& w, const Real* v, Real* out, Real
   k_project<Real><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, chi, h->d.atoms, h->d.gdv, h->wb.entries,
                                                                h->wb.n_entries, P);
   SQ_LAUNCH_CHECK(h);
-  k_apply_h<Real><<<dim3(g.nslab, w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, chi, h->d.atoms, h->wb.entries,
+  k_apply_h<Real><<<dim3(g.nbr[2], w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, chi, h->d.atoms, h->wb.entries,
                                                                h->wb.brick_list, h->wb.brick_n, vpot);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;

@@ -27,9 +27,10 @@ SQ_BOUNDS_GIVEN = 1
 SQ_N_MOMENTS = 17
 
 EXPORTED = [
-    "sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
+    "sq_setup", "sq_moments", "sq_fermi_level", "sq_node_sums", "sq_fermi_level_sums",
+    "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
-    "sq_kernel_launches", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit",
+    "sq_kernel_launches", "sq_step_launch_counts", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit",
     "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_gauss_density", "sq_green_kubo", "sq_destroy",
     "sq_last_error",
 ]
@@ -52,6 +53,7 @@ class sq_instance_desc(C.Structure):
         ("precision", C.c_int), ("bounds_mode", C.c_int),
         ("lambda_lo", C.c_double), ("lambda_hi", C.c_double),
         ("cheb_quad_M", C.c_int), ("lanczos_k", C.c_int), ("stream", C.c_void_p),
+        ("part_rank", C.c_int), ("part_count", C.c_int),
     ]
 
 
@@ -85,6 +87,10 @@ def lib():
         L.sq_setup.argtypes = [C.POINTER(sq_instance_desc), C.POINTER(H)]
         L.sq_moments.argtypes = [H]
         L.sq_fermi_level.argtypes = [H, C.POINTER(C.c_double)]
+        L.sq_node_sums.argtypes = [H, C.c_void_p]
+        L.sq_node_sums.restype = C.c_int
+        L.sq_fermi_level_sums.argtypes = [H, C.c_void_p, C.POINTER(C.c_double)]
+        L.sq_fermi_level_sums.restype = C.c_int
         L.sq_density_energy_stress.argtypes = [H, C.c_double, C.c_void_p, C.POINTER(sq_energies), C.c_void_p]
         L.sq_density_energy_stress_dev.argtypes = [H, C.c_double, C.c_void_p, C.POINTER(sq_energies), C.c_void_p]
         L.sq_pressure.argtypes = [H, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -94,6 +100,8 @@ def lib():
         L.sq_footprint_bytes.restype = C.c_size_t
         L.sq_kernel_launches.argtypes = [H]
         L.sq_kernel_launches.restype = C.c_longlong
+        L.sq_step_launch_counts.argtypes = [H, C.POINTER(C.c_longlong)]
+        L.sq_step_launch_counts.restype = C.c_int
         L.sq_kernel_timing.argtypes = [H, C.c_int]
         L.sq_kernel_timing.restype = C.c_int
         L.sq_kernel_timing_read.argtypes = [H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
@@ -133,7 +141,7 @@ def lib():
 class Desc:
     """Owns the host arrays a sq_instance_desc points to (built from a workloads dict)."""
 
-    def __init__(self, inst: dict, precision=SQ_FP64, bounds=None, stream=None, lanczos_k=0):
+    def __init__(self, inst: dict, precision=SQ_FP64, bounds=None, stream=None, lanczos_k=0, partition=None):
         self.v = np.ascontiguousarray(inst["v_eff"], dtype=np.float64)
         self.pos = np.ascontiguousarray(np.asarray(inst["pos"], dtype=np.float64).reshape(-1, 3))
         self.species = np.ascontiguousarray(inst["species"], dtype=np.int32)
@@ -171,6 +179,8 @@ class Desc:
         d.cheb_quad_M = int(inst.get("M", 2048))
         d.lanczos_k = int(lanczos_k)
         d.stream = stream
+        if partition is not None:
+            d.part_rank, d.part_count = int(partition[0]), int(partition[1])
         self.c = d
 
 
@@ -194,6 +204,81 @@ def sq_fermi_level(h) -> float:
     mu = C.c_double()
     _check(lib().sq_fermi_level(h, C.byref(mu)), h)
     return mu.value
+
+
+def sq_node_sums(h, n_pl: int) -> np.ndarray:
+    """R^j = this handle's (or partition part's) node sums of rho_q^j, j = 0..n_pl."""
+    R = np.zeros(n_pl + 1)
+    _check(lib().sq_node_sums(h, R.ctypes.data), h)
+    return R
+
+
+def sq_fermi_level_sums(h, R) -> float:
+    """Fermi level from whole-cell node sums R (e.g. the allreduce of every part's sq_node_sums)."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    mu = C.c_double()
+    _check(lib().sq_fermi_level_sums(h, R.ctypes.data, C.byref(mu)), h)
+    return mu.value
+
+
+def partition_tiles(n, rank: int, count: int, b: int = 2):
+    """The tile range [begin, end) of part `rank` of `count` (the library's rule: equal
+    contiguous ranges of the b x b x b-node tiles, t = tx + T0 (ty + T1 tz))."""
+    tiles = [(int(x) + b - 1) // b for x in n]
+    nt = tiles[0] * tiles[1] * tiles[2]
+    return nt * rank // count, nt * (rank + 1) // count
+
+
+def partition_nodes(n, rank: int, count: int, b: int = 2) -> np.ndarray:
+    """Node indices (x fastest) that part `rank` of `count` sweeps."""
+    n = [int(x) for x in n]
+    tiles = [(x + b - 1) // b for x in n]
+    t0, t1 = partition_tiles(n, rank, count, b)
+    out = []
+    for t in range(t0, t1):
+        ox, oy, oz = (t % tiles[0]) * b, ((t // tiles[0]) % tiles[1]) * b, (t // (tiles[0] * tiles[1])) * b
+        for qz in range(b):
+            for qy in range(b):
+                for qx in range(b):
+                    x, y, z = ox + qx, oy + qy, oz + qz
+                    if x < n[0] and y < n[1] and z < n[2]:
+                        out.append(x + n[0] * (y + n[1] * z))
+    return np.asarray(sorted(out), dtype=np.int64)
+
+
+# contraction outputs that add up over the parts of a node partition
+PART_SUM_KEYS = ("E_band", "E_s", "E_nl", "N_check", "E_pot", "pressure_A")
+
+
+def run_partitioned(inst: dict, precision, rank: int, count: int, allreduce, bounds=None, stream=None):
+    """One evaluation of part `rank` of `count` of the cell: the sweep over the part's tiles,
+    allreduce(R^j) (the exchange step before the Fermi search), the Fermi level, the part's
+    contraction and allreduce of the partial energies, pressure and sigma. `allreduce` maps a
+    float64 numpy vector to its sum over the parts (torch.distributed, or any callable)."""
+    d = Desc(inst, precision, bounds, stream, partition=(rank, count))
+    h = sq_setup(d)
+    try:
+        sq_moments(h)
+        n_pl = int(inst["n_pl"])
+        R = allreduce(sq_node_sums(h, n_pl))
+        mu = sq_fermi_level_sums(h, R)
+        nd = int(np.prod(inst["n"]))
+        rho, en, sig = sq_density_energy_stress(h, mu, nd)
+        p_a, e_pot = sq_pressure(h, mu)
+        part = dict(en)
+        part["pressure_A"], part["E_pot"] = p_a, e_pot
+        vec = np.concatenate([[part[k] for k in PART_SUM_KEYS], np.asarray(sig).reshape(9)])
+        tot = allreduce(vec)
+        out = {k: float(tot[i]) for i, k in enumerate(PART_SUM_KEYS)}
+        out["F"] = out["E_band"] + out["E_s"]
+        out["sigma"] = np.asarray(tot[len(PART_SUM_KEYS):]).reshape(3, 3)
+        out["mu"] = mu
+        out["rho_part"] = rho
+        out["R"] = R
+        out["bounds"] = sq_get_bounds(h)
+        return out
+    finally:
+        sq_destroy(h)
 
 
 def sq_density_energy_stress(h, mu: float, nd: int | None = None):
@@ -241,6 +326,14 @@ def sq_kernel_launches(h) -> int:
     return int(lib().sq_kernel_launches(h))
 
 
+def sq_step_launch_counts(h):
+    """Step-kernel launches by variant: (shared memory + tensor cores, shared memory + scalar,
+    global-memory projections)."""
+    c = (C.c_longlong * 3)()
+    _check(lib().sq_step_launch_counts(h, c), h)
+    return tuple(int(x) for x in c)
+
+
 def sq_kernel_timing(h, enable: bool):
     _check(lib().sq_kernel_timing(h, 1 if enable else 0), h)
 
@@ -282,7 +375,8 @@ def run(inst: dict, precision=SQ_FP64, bounds=None, want_moments=False, stream=N
         rho, en, sig = sq_density_energy_stress(h, mu, nd)
         p_a, e_pot = sq_pressure(h, mu)
         out = {"mu": mu, "rho": rho, "sigma": sig, "bounds": sq_get_bounds(h),
-               "launches": sq_kernel_launches(h), "pressure_A": p_a, "E_pot": e_pot}
+               "launches": sq_kernel_launches(h), "pressure_A": p_a, "E_pot": e_pot,
+               "step_variants": sq_step_launch_counts(h)}
         out.update(en)
         if want_moments:
             out["moments"] = sq_moments_copy(h, nd, int(inst["n_pl"]))
