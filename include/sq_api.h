@@ -67,6 +67,11 @@ extern "C" {
 /* spectral bound modes (the paper takes chi, zeta from the extreme eigenvalues of H_q) */
 #define SQ_BOUNDS_LANCZOS 0   /* k-step Lanczos on sample regions, widened (default)   */
 #define SQ_BOUNDS_GIVEN 1     /* lambda_lo / lambda_hi taken from the descriptor        */
+#define SQ_BOUNDS_PER_NODE 2  /* Sec. 4 literally: chi_q, zeta_q from the extreme eigenvalues
+                                 of each node's own H_q (k-step Lanczos on every node, widened
+                                 as the shared interval); the Fermi search and the contraction
+                                 use each node's own coefficients c_q^j(mu), d_q^j, s_q^j.
+                                 Not combined with a node partition.                      */
 
 /* Moments per node and Chebyshev index (sq_moments_copy layout) */
 #define SQ_N_MOMENTS 17  /* rho, K_xx K_yy K_zz K_yz K_xz K_xy, N, S_ab (8 + 3a + b) */
@@ -141,6 +146,17 @@ int sq_moments(sq_handle* h);
  * SQ_ERR_NO_BRACKET, SQ_ERR_CUDA. */
 int sq_fermi_level(sq_handle* h, double* mu_out);
 
+/* Resident state for a trajectory (successive quantum-MD snapshots of one cell): gives the
+ * handle new atom positions pos [n_atoms][3] and a new V_eff [N_d] (host, copied before
+ * return) for the same cell, grid, species and projectors. The device buffers, stream and
+ * projector-table slots of the handle are kept (each atom's table slot is sized at sq_setup
+ * for any position); the base images, support boxes and projector tables are rebuilt, and
+ * with SQ_BOUNDS_LANCZOS the bounds are recomputed by the next sq_moments (sample tiles from
+ * the new V_eff). Results equal those of a fresh sq_setup of the new snapshot. The moments
+ * must be recomputed (sq_moments) before the Fermi level or a contraction. Synchronises.
+ * Errors: SQ_ERR_INVALID_ARG (NULL or non-finite input), SQ_ERR_CUDA. */
+int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff);
+
 /* Node partition (part_count > 0): the moments of the nodes outside the handle's tile range
  * are zero, so R^j and every contraction output are this part's share of the node sums of
  * Sec. 4, and the parts add up to the whole cell. The Fermi level needs the whole-cell sums:
@@ -180,8 +196,15 @@ int sq_density_energy_stress_dev(sq_handle* h, double mu, double* rho_dev, sq_en
  * Errors: SQ_ERR_STATE (no moments), SQ_ERR_INVALID_ARG (NULL pressure_out, non-finite mu). */
 int sq_pressure(sq_handle* h, double mu, double* pressure_out, double* e_pot_out);
 
-/* Bounds in use (after sq_moments in Lanczos mode). */
+/* Bounds in use (after sq_moments in Lanczos mode); in SQ_BOUNDS_PER_NODE mode the smallest
+ * lower and the largest upper node bound. */
 int sq_get_bounds(const sq_handle* h, double* lambda_lo, double* lambda_hi);
+
+/* SQ_BOUNDS_PER_NODE: every node's effective interval [lo_q, hi_q] (host, [N_d] each, x fastest)
+ * after sq_moments: the one the recurrence realises (chi_q -+ zeta_q after the FP32-exact
+ * scaling of SQ_MIXED and the stencil's constant-mode offset), which the Fermi search and the
+ * contraction use. Errors: SQ_ERR_INVALID_ARG (NULL, other bounds modes), SQ_ERR_STATE. */
+int sq_node_bounds(sq_handle* h, double* lo_out, double* hi_out);
 
 /* Copies the moment table [N_d][n_pl + 1][SQ_N_MOMENTS] (FP64, host) for inspection. */
 int sq_moments_copy(sq_handle* h, double* host_out);
@@ -254,7 +277,8 @@ int sq_batch_evaluate(sq_handle* const* hs, int n, int max_concurrent, double* m
 /* Request loop with continuous batching (one GPU). Requests are admitted in submission order
  * as soon as their device footprint (sq_footprint_bytes) fits under hbm_budget_bytes next to
  * those in flight and fewer than max_inflight run; each admitted request runs setup, moments,
- * Fermi level and contraction on its own stream and host thread and is destroyed afterwards.
+ * Fermi level and contraction on its own stream and host thread and is destroyed afterwards
+ * (see sq_server_submit_traj for requests that keep their state on the device).
  * A request larger than the whole budget completes with status SQ_ERR_OOM. */
 typedef struct sq_server sq_server;
 typedef struct {
@@ -273,8 +297,21 @@ int sq_server_submit(sq_server* s, const sq_instance_desc* desc, long long tag);
 /* Moves up to max_results finished results to out (host), waiting up to timeout_ms for the
  * first one; *n_out receives the count. */
 int sq_server_poll(sq_server* s, sq_result* out, int max_results, int timeout_ms, int* n_out);
+/* A request that belongs to trajectory traj (>= 0): successive snapshots of one cell (same
+ * grid, species, projectors, kT, n_e, r_cut, n_pl, precision and bounds mode; new positions
+ * and V_eff). The trajectory's first request sets up a handle that stays resident on the device;
+ * its later requests move that handle's atoms in place (sq_update_atoms) instead of setting up
+ * and destroying one, and run one at a time in submission order (requests of other
+ * trajectories may go ahead of a request whose trajectory is busy). A request whose other
+ * fields differ from the resident handle's replaces it. Idle resident handles count against
+ * hbm_budget_bytes and are released, least recently used first, when a request needs the
+ * memory, and all of them by sq_server_destroy. Errors: as sq_server_submit; traj < 0 is
+ * SQ_ERR_INVALID_ARG. */
+int sq_server_submit_traj(sq_server* s, const sq_instance_desc* desc, long long tag, long long traj);
 /* Requests queued or running (-1 for NULL). */
 int sq_server_pending(sq_server* s);
+/* Trajectory handles resident on the device (-1 for NULL). */
+int sq_server_resident(sq_server* s);
 /* Stops admitting, finishes every queued and running request, frees the server (results not
  * polled are dropped). */
 void sq_server_destroy(sq_server* s);

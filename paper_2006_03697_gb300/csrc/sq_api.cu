@@ -39,6 +39,26 @@ void fd_weights(int n_o, double* w, double* g) {
   w[0] = -2.0 * s;
 }
 
+// Largest number of lattice points of spacing h in an interval of length 2 rc (the support
+// box extent of an atom of radius rc on that axis, wherever the atom sits), plus one point of
+// slack against rounding in the floor / ceil of place_atom.
+int box_extent_max(double rc, double h) { return int(std::floor(2.0 * rc / h + 1e-9)) + 2; }
+
+// An atom's base image (position wrapped into the cell) and its support box for radius rc:
+// the lattice points lo_a .. lo_a + dim_a - 1 with |x_a - R_a| <= rc on each axis.
+void place_atom(const sq::Geo& g, double rc, const double* pos, sq::AtomTab& at) {
+  for (int a = 0; a < 3; ++a) {
+    double R = pos[a];
+    R -= std::floor(R / g.L[a]) * g.L[a];
+    if (R >= g.L[a]) R -= g.L[a];
+    at.R[a] = R;
+    at.lo[a] = int(std::ceil((R - rc) / g.h[a]));
+    const int hi = int(std::floor((R + rc) / g.h[a]));
+    at.dim[a] = std::min(std::max(0, hi - at.lo[a] + 1), box_extent_max(rc, g.h[a]));
+    at.dlo[a] = float(at.lo[a] * g.h[a] - R);
+  }
+}
+
 int validate(const sq_instance_desc* d, std::string& why) {
   if (!d) { why = "desc is NULL"; return SQ_ERR_INVALID_ARG; }
   for (int a = 0; a < 3; ++a) {
@@ -84,7 +104,12 @@ int validate(const sq_instance_desc* d, std::string& why) {
   if (d->lanczos_k > 128) { why = "lanczos_k must be <= 128"; return SQ_ERR_INVALID_ARG; }
   if (d->cheb_quad_M > 6144) { why = "cheb_quad_M must be <= 6144"; return SQ_ERR_INVALID_ARG; }
   if (d->precision != SQ_FP64 && d->precision != SQ_MIXED) { why = "unknown precision"; return SQ_ERR_INVALID_ARG; }
-  if (d->bounds_mode != SQ_BOUNDS_LANCZOS && d->bounds_mode != SQ_BOUNDS_GIVEN) { why = "unknown bounds mode"; return SQ_ERR_INVALID_ARG; }
+  if (d->bounds_mode != SQ_BOUNDS_LANCZOS && d->bounds_mode != SQ_BOUNDS_GIVEN && d->bounds_mode != SQ_BOUNDS_PER_NODE) {
+    why = "unknown bounds mode"; return SQ_ERR_INVALID_ARG;
+  }
+  if (d->bounds_mode == SQ_BOUNDS_PER_NODE && d->part_count > 0) {
+    why = "per-node bounds are not combined with a node partition"; return SQ_ERR_INVALID_ARG;
+  }
   if (d->part_count < 0 || (d->part_count > 0 && (d->part_rank < 0 || d->part_rank >= d->part_count))) {
     why = "partition needs 0 <= part_rank < part_count (or part_count = 0)"; return SQ_ERR_INVALID_ARG;
   }
@@ -108,7 +133,43 @@ struct Plan {
   size_t per_tile_bytes = 0;
   size_t fixed_bytes = 0;
   int tile_begin = 0, tile_end = 0;   // the tiles this handle sweeps (the node partition)
+  int lz_cap = 0;                     // most Lanczos sample tiles any V_eff can select
+  int nlz_wave = 0;                   // tiles per Lanczos wave of the per-node bounds
 };
+
+// Sample nodes of the Lanczos bounds: argmin V, argmax V and a stride-n/2 node grid; their
+// tiles, without repeats, in that order.
+std::vector<int> lanczos_sample_tiles(const sq::Geo& g, const double* v) {
+  const long long Nd = (long long)g.n[0] * g.n[1] * g.n[2];
+  std::vector<int> seeds, tiles;
+  int imin = 0, imax = 0;
+  for (long long i = 1; i < Nd; ++i) {
+    if (v[i] < v[imin]) imin = int(i);
+    if (v[i] > v[imax]) imax = int(i);
+  }
+  seeds.push_back(imin);
+  seeds.push_back(imax);
+  int st[3];
+  for (int a = 0; a < 3; ++a) st[a] = std::max(1, g.n[a] / 2);
+  for (int iz = 0; iz < g.n[2]; iz += st[2])
+    for (int iy = 0; iy < g.n[1]; iy += st[1])
+      for (int ix = 0; ix < g.n[0]; ix += st[0]) seeds.push_back(ix + g.n[0] * (iy + g.n[1] * iz));
+  for (int q : seeds) {
+    const int ix = q % g.n[0], iy = (q / g.n[0]) % g.n[1], iz = q / (g.n[0] * g.n[1]);
+    const int t = ix / g.b + g.tiles[0] * (iy / g.b + g.tiles[1] * (iz / g.b));
+    if (std::find(tiles.begin(), tiles.end(), t) == tiles.end()) tiles.push_back(t);
+  }
+  return tiles;
+}
+
+int lanczos_sample_cap(const sq::Geo& g) {
+  int grid = 1;
+  for (int a = 0; a < 3; ++a) {
+    const int st = std::max(1, g.n[a] / 2);
+    grid *= (g.n[a] + st - 1) / st;
+  }
+  return std::min(2 + grid, g.n_tiles);
+}
 
 int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   sq::Geo& g = P.geo;
@@ -188,29 +249,25 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
         ch++;
       }
     }
-    long long boxpts = 1;
+    place_atom(g, rc_max, d->pos + 3 * J, at);
+    // every atom owns a fixed table slot sized for the largest support box its radius allows
+    // anywhere in the cell, so a handle can take new positions in place (sq_update_atoms)
+    int dmax[3];
+    long long slot = 1;
     for (int a = 0; a < 3; ++a) {
-      double R = d->pos[3 * J + a];
-      R -= std::floor(R / g.L[a]) * g.L[a];
-      if (R >= g.L[a]) R -= g.L[a];
-      at.R[a] = R;
-      at.lo[a] = int(std::ceil((R - rc_max) / g.h[a]));
-      int hi = int(std::floor((R + rc_max) / g.h[a]));
-      at.dim[a] = std::max(0, hi - at.lo[a] + 1);
-      at.dlo[a] = float(at.lo[a] * g.h[a] - R);
-      boxpts *= at.dim[a];
+      dmax[a] = box_extent_max(rc_max, g.h[a]);
+      slot *= dmax[a];
     }
-    if (at.nch == 0) boxpts = 0;
+    if (at.nch == 0) slot = 0;
     P.rcmax.push_back(rc_max);
     at.nchp = (at.nch + 3) / 4 * 4;
     at.off = off;
-    off += boxpts * at.nchp;
+    off += slot * at.nchp;
     // capacity bounds: images of this atom that can meet a window of extent W on axis a
     long long nimg_u = 1, nimg_b = 1;
     for (int a = 0; a < 3; ++a) {
-      if (at.dim[a] == 0) { nimg_u = nimg_b = 0; break; }
-      nimg_u *= floor_div(g.U[a] + at.dim[a] - 2, g.n[a]) + 1;
-      nimg_b *= floor_div(sq::kBrick + at.dim[a] - 2, g.n[a]) + 1;
+      nimg_u *= floor_div(g.U[a] + dmax[a] - 2, g.n[a]) + 1;
+      nimg_b *= floor_div(sq::kBrick + dmax[a] - 2, g.n[a]) + 1;
     }
     if (at.nch == 0) { nimg_u = nimg_b = 0; }
     e_cap += nimg_u;
@@ -246,29 +303,14 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
                   size_t(Nd) * size_t(d->n_pl + 1) * SQ_N_MOMENTS * sizeof(double) +   // moments
                   size_t(d->n_pl + 1) * 4 * sizeof(double) + size_t(M) * sizeof(double) +
                   size_t(Nd) * sizeof(double) + 4096 * 32 * sizeof(double) + 1024;
-  // Lanczos sample tiles: the tiles holding argmin V, argmax V and a stride-n/2 node grid
+  // Lanczos sample tiles (argmin V, argmax V, a stride-n/2 node grid); the buffers hold the
+  // largest count so that sq_update_atoms can move them with V
   P.lz_tiles.clear();
   if (d->bounds_mode == SQ_BOUNDS_LANCZOS) {
-    std::vector<int> seeds;
-    int imin = 0, imax = 0;
-    for (long long i = 1; i < Nd; ++i) {
-      if (d->v_eff[i] < d->v_eff[imin]) imin = int(i);
-      if (d->v_eff[i] > d->v_eff[imax]) imax = int(i);
-    }
-    seeds.push_back(imin);
-    seeds.push_back(imax);
-    int st[3];
-    for (int a = 0; a < 3; ++a) st[a] = std::max(1, g.n[a] / 2);
-    for (int iz = 0; iz < g.n[2]; iz += st[2])
-      for (int iy = 0; iy < g.n[1]; iy += st[1])
-        for (int ix = 0; ix < g.n[0]; ix += st[0]) seeds.push_back(ix + g.n[0] * (iy + g.n[1] * iz));
-    for (int q : seeds) {
-      const int ix = q % g.n[0], iy = (q / g.n[0]) % g.n[1], iz = q / (g.n[0] * g.n[1]);
-      const int t = ix / g.b + g.tiles[0] * (iy / g.b + g.tiles[1] * (iz / g.b));
-      if (std::find(P.lz_tiles.begin(), P.lz_tiles.end(), t) == P.lz_tiles.end()) P.lz_tiles.push_back(t);
-    }
+    P.lz_tiles = lanczos_sample_tiles(g, d->v_eff);
+    P.lz_cap = lanczos_sample_cap(g);
     const int k = d->lanczos_k > 0 ? d->lanczos_k : 40;
-    const size_t nst = P.lz_tiles.size();
+    const size_t nst = size_t(P.lz_cap);
     P.fixed_bytes += sizeof(double) * (size_t(k + 2) * nst * g.Upts * g.B + nst * size_t(g.r_cap) * g.B +
                                        nst * g.B * size_t(5 * k + 8)) + sizeof(int) * nst;
   }
@@ -287,7 +329,16 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   wc = std::min<long long>(std::min<long long>(wc, ntl), 32768);
   const long long nwaves = (ntl + wc - 1) / wc;
   P.wave_cap = int((ntl + nwaves - 1) / nwaves);
-  P.wave_cap = std::max<int>(P.wave_cap, int(P.lz_tiles.size()));
+  P.wave_cap = std::max<int>(P.wave_cap, P.lz_cap);
+  if (d->bounds_mode == SQ_BOUNDS_PER_NODE) {
+    // every node's own Lanczos: waves of tiles with k + 2 Krylov vectors each under 8 GiB, the
+    // per-node interval and step coefficients, the Fermi-search cosine sums and contraction rows
+    const int k = d->lanczos_k > 0 ? d->lanczos_k : 40;
+    const size_t per_tile = (size_t(k + 2) * g.Upts + size_t(g.r_cap)) * g.B * real + size_t(g.B) * (5 * k + 8) * 8;
+    P.nlz_wave = int(std::max<size_t>(1, std::min<size_t>((size_t(8) << 30) / per_tile, size_t(P.wave_cap))));
+    P.fixed_bytes += size_t(P.nlz_wave) * per_tile + size_t(Nd) * (4 + M + 20) * sizeof(double) +
+                     size_t(4 * M + 1024) * sizeof(double);
+  }
   return SQ_OK;
 }
 }  // namespace
@@ -422,6 +473,9 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   h->vol = desc->L[0] * desc->L[1] * desc->L[2];
   h->stream = (cudaStream_t)desc->stream;
   h->atoms_h = P.atoms;
+  h->rcmax_h = P.rcmax;
+  h->lz_cap = P.lz_cap;
+  h->nlz_wave = P.nlz_wave;
   h->proj4 = true;
   for (const sq::AtomTab& at : P.atoms) h->proj4 = h->proj4 && at.nchp <= 4;
   h->table_len = P.table_len;
@@ -492,13 +546,27 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->wb.Pg[1], sizeof(double) * size_t(wt) * g.r_cap * g.B);
   SQ_ALLOC(h->wb.Spart, sizeof(double) * size_t(wt) * g.nslab * g.B * 9);
   if (!h->lanczos_tiles.empty()) {
-    const size_t nst = h->lanczos_tiles.size();
+    const size_t nst = size_t(P.lz_cap);
     const int k = h->lanczos_k;
     SQ_ALLOC(h->d.lzV, sizeof(double) * size_t(k + 1) * nst * g.Upts * g.B);
     SQ_ALLOC(h->d.lzW, sizeof(double) * nst * g.Upts * g.B);
     SQ_ALLOC(h->d.lzP, sizeof(double) * nst * size_t(g.r_cap) * g.B);
     SQ_ALLOC(h->d.lzC, sizeof(double) * nst * g.B * size_t(5 * k + 8));
     SQ_ALLOC(h->d.lz_tiles, sizeof(int) * nst);
+  }
+  if (h->bounds_mode == SQ_BOUNDS_PER_NODE) {
+    const int k = h->lanczos_k;
+    const size_t nw = size_t(h->nlz_wave);
+    SQ_ALLOC(h->d.nbnd, sizeof(double) * 2 * size_t(Nd));
+    SQ_ALLOC(h->d.ncoef, sizeof(double) * 2 * size_t(Nd));
+    SQ_ALLOC(h->d.nF, sizeof(double) * size_t(Nd) * h->M);
+    SQ_ALLOC(h->d.nrow, sizeof(double) * size_t(Nd) * 20);
+    SQ_ALLOC(h->d.costab, sizeof(double) * 4 * size_t(h->M));
+    SQ_ALLOC(h->d.npart, sizeof(double) * 1024);
+    SQ_ALLOC(h->d.nV, real * size_t(k + 1) * nw * g.Upts * g.B);
+    SQ_ALLOC(h->d.nW, real * nw * g.Upts * g.B);
+    SQ_ALLOC(h->d.nP, real * nw * size_t(g.r_cap) * g.B);
+    SQ_ALLOC(h->d.nC, sizeof(double) * nw * g.B * size_t(5 * k + 8));
   }
 #undef SQ_ALLOC
 
@@ -563,6 +631,10 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   }
   rc = sq::build_tables(h);
   if (rc != SQ_OK) return cleanup(rc);
+  if (h->bounds_mode == SQ_BOUNDS_PER_NODE) {
+    rc = sq::init_node_tables(h);
+    if (rc != SQ_OK) return cleanup(rc);
+  }
 
   *out = h;
   return SQ_OK;
@@ -575,6 +647,10 @@ int sq_moments(sq_handle* h) {
     rc = sq::run_lanczos(h);
     if (rc != SQ_OK) return rc;
     h->bounds_ready = true;
+  } else if (h->bounds_mode == SQ_BOUNDS_PER_NODE) {
+    rc = sq::run_lanczos_nodes(h);
+    if (rc != SQ_OK) return rc;
+    h->bounds_ready = true;
   }
   rc = sq::run_sweep(h);
   if (rc != SQ_OK) return rc;
@@ -585,7 +661,43 @@ int sq_moments(sq_handle* h) {
 int sq_fermi_level(sq_handle* h, double* mu_out) {
   if (!h) return SQ_ERR_INVALID_ARG;
   if (!h->moments_ready) return sq::fail(h, SQ_ERR_STATE, "sq_fermi_level before sq_moments");
+  if (h->bounds_mode == SQ_BOUNDS_PER_NODE) return sq::run_fermi_nodes(h, mu_out);
   return sq::run_fermi(h, mu_out);
+}
+
+int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff) {
+  if (!h) return SQ_ERR_INVALID_ARG;
+  const sq::Geo& g = h->geo;
+  if (!v_eff || (g.n_atoms > 0 && !pos)) return sq::fail(h, SQ_ERR_INVALID_ARG, "pos or v_eff is NULL");
+  for (int i = 0; i < h->Nd; ++i)
+    if (!std::isfinite(v_eff[i])) return sq::fail(h, SQ_ERR_INVALID_ARG, "v_eff has a non-finite value");
+  for (int i = 0; i < 3 * g.n_atoms; ++i)
+    if (!std::isfinite(pos[i])) return sq::fail(h, SQ_ERR_INVALID_ARG, "non-finite atom position");
+  // new base images and support boxes inside each atom's fixed table slot
+  for (int J = 0; J < g.n_atoms; ++J) place_atom(g, h->rcmax_h[J], pos + 3 * J, h->atoms_h[J]);
+  cudaStream_t s = h->stream;
+  std::vector<float> v32(h->Nd);
+  for (int i = 0; i < h->Nd; ++i) v32[i] = float(v_eff[i]);
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.v64, v_eff, sizeof(double) * h->Nd, cudaMemcpyHostToDevice, s));
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.v32, v32.data(), sizeof(float) * h->Nd, cudaMemcpyHostToDevice, s));
+  if (g.n_atoms > 0)
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.atoms, h->atoms_h.data(), sizeof(sq::AtomTab) * h->atoms_h.size(),
+                                   cudaMemcpyHostToDevice, s));
+  if (h->bounds_mode == SQ_BOUNDS_LANCZOS) {
+    // the sample tiles follow argmin / argmax of the new V_eff
+    std::vector<int> lz = lanczos_sample_tiles(g, v_eff);
+    if (int(lz.size()) > h->lz_cap) return sq::fail(h, SQ_ERR_STATE, "Lanczos sample capacity exceeded");
+    h->lanczos_tiles = lz;
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.lz_tiles, lz.data(), sizeof(int) * lz.size(), cudaMemcpyHostToDevice, s));
+    h->bounds_ready = false;
+  }
+  const int rc = sq::build_tables(h);
+  if (rc != SQ_OK) return rc;
+  // pageable host sources: the copies have read them before the call returns; the handle's
+  // results now describe the new snapshot only after the next sq_moments
+  SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+  h->moments_ready = false;
+  return SQ_OK;
 }
 
 int sq_node_sums(sq_handle* h, double* R_out) {
@@ -600,6 +712,8 @@ int sq_fermi_level_sums(sq_handle* h, const double* R_host, double* mu_out) {
   for (int j = 0; j <= h->geo.n_pl; ++j)
     if (!std::isfinite(R_host[j])) return sq::fail(h, SQ_ERR_INVALID_ARG, "R_host has a non-finite value");
   if (!h->bounds_ready) return sq::fail(h, SQ_ERR_STATE, "sq_fermi_level_sums before the bounds are known");
+  if (h->bounds_mode == SQ_BOUNDS_PER_NODE)
+    return sq::fail(h, SQ_ERR_STATE, "node sums carry no per-node coefficients (SQ_BOUNDS_PER_NODE)");
   return sq::run_fermi_sums(h, R_host, mu_out);
 }
 
@@ -609,7 +723,9 @@ static int contraction_common(sq_handle* h, double mu, double* rho_dev, sq_energ
   if (!h->moments_ready) return sq::fail(h, SQ_ERR_STATE, "contraction before sq_moments");
   if (!std::isfinite(mu)) return sq::fail(h, SQ_ERR_INVALID_ARG, "mu is not finite");
   double out[16];
-  int rc = sq::run_contraction(h, mu, rho_dev, (e_out || sigma_host || pressure_host) ? out : nullptr);
+  double* sums = (e_out || sigma_host || pressure_host) ? out : nullptr;
+  int rc = (h->bounds_mode == SQ_BOUNDS_PER_NODE) ? sq::run_contraction_nodes(h, mu, rho_dev, sums)
+                                                  : sq::run_contraction(h, mu, rho_dev, sums);
   if (rc != SQ_OK) return rc;
   if (pressure_host) {
     pressure_host[0] = out[14];
@@ -661,6 +777,20 @@ int sq_get_bounds(const sq_handle* h, double* lo, double* hi) {
   if (!h->bounds_ready) return SQ_ERR_STATE;
   *lo = h->lam_lo;
   *hi = h->lam_hi;
+  return SQ_OK;
+}
+
+int sq_node_bounds(sq_handle* h, double* lo_out, double* hi_out) {
+  if (!h || !lo_out || !hi_out) return SQ_ERR_INVALID_ARG;
+  if (h->bounds_mode != SQ_BOUNDS_PER_NODE) return sq::fail(h, SQ_ERR_INVALID_ARG, "not in per-node bounds mode");
+  if (!h->bounds_ready) return sq::fail(h, SQ_ERR_STATE, "no per-node bounds yet");
+  std::vector<double> b(2 * size_t(h->Nd));
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(b.data(), h->d.nbnd, sizeof(double) * b.size(), cudaMemcpyDeviceToHost, h->stream));
+  SQ_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (int q = 0; q < h->Nd; ++q) {
+    lo_out[q] = b[2 * q];
+    hi_out[q] = b[2 * q + 1];
+  }
   return SQ_OK;
 }
 

@@ -137,6 +137,17 @@ struct Dev {
   double* lzP = nullptr;          // projections of the Lanczos vector [nst][r_cap][B]
   double* lzC = nullptr;          // Gram-Schmidt coefficients / alpha, beta [cols][...]
   int* lz_tiles = nullptr;        // sample tile ids [nst]
+  // per-node bounds mode (SQ_BOUNDS_PER_NODE)
+  double* nbnd = nullptr;         // [N_d][2] effective (lo, hi) of every node
+  double* ncoef = nullptr;        // [N_d][2] step coefficients (ca = 2 / zeta_q, cd = ca lap0 - 2 chi_q / zeta_q)
+  double* nF = nullptr;           // [N_d][M] sum'_j cos(j theta_k) rho_q^j
+  double* nrow = nullptr;         // [N_d][20] contraction terms per node
+  double* costab = nullptr;       // [4 M] cos(pi t / (2 M))
+  double* npart = nullptr;        // [1024] partial electron counts
+  void* nV = nullptr;             // Lanczos wave buffers of the per-node bounds
+  void* nW = nullptr;
+  void* nP = nullptr;
+  double* nC = nullptr;
 };
 
 }  // namespace sq
@@ -158,6 +169,9 @@ struct sq_handle {
   double vol = 0;
   cudaStream_t stream = nullptr;
   std::vector<sq::AtomTab> atoms_h;
+  std::vector<double> rcmax_h;      // per atom: support radius (its table slot is sized for it)
+  int lz_cap = 0;                   // Lanczos sample-tile capacity of the buffers
+  int nlz_wave = 0;                 // tiles per Lanczos wave of the per-node bounds
   long long table_len = 0;
   int n_ch_total = 0;
   bool proj4 = false;               // every atom has at most 4 projector channels (one group per image)
@@ -214,6 +228,7 @@ int timing_collect(sq_handle* h);
 
 // setup kernels (sq_setup.cu)
 int build_tables(sq_handle* h);
+int init_node_tables(sq_handle* h);   // per-node bounds mode: cosine table, neutral node bounds
 int build_wave_lists(sq_handle* h, const Wave& w);
 
 // sweep (sq_sweep.cu)
@@ -232,6 +247,10 @@ int run_lanczos(sq_handle* h);
 template <typename Real>
 int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C);
 int run_fermi(sq_handle* h, double* mu_out);
+// per-node bounds mode (sq_lanczos.cu, sq_reduce.cu)
+int run_lanczos_nodes(sq_handle* h);
+int run_fermi_nodes(sq_handle* h, double* mu_out);
+int run_contraction_nodes(sq_handle* h, double mu, double* rho_dev, double* sums_host);
 int run_node_sums(sq_handle* h, double* R_out);
 int run_fermi_sums(sq_handle* h, const double* R_host, double* mu_out);
 int run_contraction(sq_handle* h, double mu, double* rho_dev, double* sums_host);

@@ -10,6 +10,10 @@
 // then widened by 1 % of its width on each side. One interval serves every node (every H_q
 // is a principal submatrix of the infinite-crystal H, so a shared interval is valid for all
 // of them when it contains the sampled spectra with margin).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "sq_device.cuh"
 
 namespace sq {
@@ -230,6 +234,72 @@ __global__ void k_lz_bounds(int ncols, int k, const double* __restrict__ alpha, 
   }
 }
 
+// The per-node bounds mode: each column's own interval (Ritz extremes widened by their residual
+// norms, then by 1 % of that column's width, as the shared interval is formed from all sample
+// columns) and the step coefficients the recurrence of that node uses, with the scaling rules
+// of set_bounds (SQ_MIXED: FP32-exact 2 / zeta and -2 chi / zeta; the diagonal coefficient
+// rounded once; the stencil's constant-mode offset and that rounding folded into the centre).
+__global__ void k_lz_node_bounds(Geo g, Wave w, int k, const double* __restrict__ alpha, const double* __restrict__ beta,
+                                 const int* __restrict__ keff, int mixed, double lap_offset, double* __restrict__ nbnd,
+                                 double* __restrict__ ncoef) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= w.ntiles * g.B) return;
+  int o[3], qo[3];
+  tile_origin(g, wave_tile(w, col / g.B), o);
+  node_offset(g, col % g.B, qo);
+  if (!node_valid(g, o, qo)) return;
+  const int node = (o[0] + qo[0]) + g.n[0] * ((o[1] + qo[1]) + g.n[1] * (o[2] + qo[2]));
+  const int n = keff[col];
+  if (n <= 0) return;
+  double y[kMaxLanczos], dd[kMaxLanczos];
+  const double* a = alpha + (size_t)col * k;
+  const double* b = beta + (size_t)col * k;
+  double gl = INFINITY, gu = -INFINITY;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < n - 1 ? fabs(b[i]) : 0.0);
+    gl = fmin(gl, a[i] - r);
+    gu = fmax(gu, a[i] + r);
+  }
+  double l = gl, u = gu;
+  for (int it = 0; it < 200 && u - l > 1e-15 * fmax(1.0, fmax(fabs(l), fabs(u))); ++it) {
+    const double mid = 0.5 * (l + u);
+    if (sturm_count(a, b, n, mid) >= 1) u = mid; else l = mid;
+  }
+  const double tmin = 0.5 * (l + u);
+  l = gl;
+  u = gu;
+  for (int it = 0; it < 200 && u - l > 1e-15 * fmax(1.0, fmax(fabs(l), fabs(u))); ++it) {
+    const double mid = 0.5 * (l + u);
+    if (sturm_count(a, b, n, mid) >= n) u = mid; else l = mid;
+  }
+  const double tmax = 0.5 * (l + u);
+  const double bl = fabs(b[n - 1]);
+  const double del = 1e-10 * fmax(gu - gl, 1e-300);
+  const double rmin = (n > 1) ? bl * last_component(a, b, n, tmin - del, y, dd) : bl;
+  const double rmax = (n > 1) ? bl * last_component(a, b, n, tmax + del, y, dd) : bl;
+  double lo = tmin - rmin, hi = tmax + rmax;
+  const double wdt = hi - lo;
+  lo -= 0.01 * wdt;
+  hi += 0.01 * wdt;
+  // scaling of this node's recurrence (set_bounds, per node)
+  double chi = 0.5 * (hi + lo), zeta = 0.5 * (hi - lo);
+  double ca = 2.0 / zeta, cb = -2.0 * chi / zeta;
+  if (mixed) {
+    ca = double(float(ca));
+    zeta = 2.0 / ca;
+    cb = double(float(-2.0 * chi / zeta));
+    chi = -cb * zeta / 2.0;
+  }
+  double cd = ca * g.lap0 + cb;
+  if (mixed) cd = double(float(cd));
+  const double eps = cd - (ca * g.lap0 + cb);
+  chi -= lap_offset + eps / ca;
+  nbnd[2 * node] = chi - zeta;
+  nbnd[2 * node + 1] = chi + zeta;
+  ncoef[2 * node] = ca;
+  ncoef[2 * node + 1] = cd;
+}
+
 // k-step Lanczos (CGS2 reorthogonalisation) of every node column of the wave's tiles, from the
 // hash start vector (start = 0, the spectral bounds) or from e_q (start = 1, Gauss SQ). V holds
 // k + 1 vectors of the wave, W one, P the projections; C is (5 k + 8) doubles per column:
@@ -313,6 +383,46 @@ static int run_lanczos_t(sq_handle* h) {
   if (!(b2[0] < b2[1]) || !std::isfinite(b2[0]) || !std::isfinite(b2[1]))
     return fail(h, SQ_ERR_CUDA, "Lanczos bounds are not finite");
   return set_bounds(h, b2[0], b2[1]);
+}
+
+// Per-node bounds: every node column of the handle's tiles, in waves of nlz_wave tiles.
+template <typename Real>
+static int run_lanczos_nodes_t(sq_handle* h) {
+  const Geo& g = h->geo;
+  const int k = h->lanczos_k;
+  for (int t0 = h->tile_begin; t0 < h->tile_end; t0 += h->nlz_wave) {
+    const Wave w{t0, std::min(h->nlz_wave, h->tile_end - t0), nullptr};
+    int rc = lanczos_columns<Real>(h, w, 0, k, reinterpret_cast<Real*>(h->d.nV), reinterpret_cast<Real*>(h->d.nW),
+                                   reinterpret_cast<Real*>(h->d.nP), h->d.nC);
+    if (rc != SQ_OK) return rc;
+    const int ncols = w.ntiles * g.B;
+    const double* alpha = h->d.nC + (size_t)3 * ncols * (k + 1);
+    const double* beta = alpha + (size_t)ncols * k;
+    const int* keff = (const int*)(beta + (size_t)ncols * k);
+    k_lz_node_bounds<<<(ncols + 63) / 64, 64, 0, h->stream>>>(g, w, k, alpha, beta, keff, h->precision == SQ_MIXED,
+                                                               h->lap_offset, h->d.nbnd, h->d.ncoef);
+    SQ_LAUNCH_CHECK(h);
+  }
+  // the extreme node bounds (sq_get_bounds)
+  std::vector<double> b(2 * size_t(h->Nd));
+  SQ_CUDA_TRY(h, cudaMemcpyAsync(b.data(), h->d.nbnd, sizeof(double) * b.size(), cudaMemcpyDeviceToHost, h->stream));
+  SQ_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  double lo = INFINITY, hi = -INFINITY;
+  for (int q = 0; q < h->Nd; ++q) {
+    if (!(b[2 * q] < b[2 * q + 1]) || !std::isfinite(b[2 * q]) || !std::isfinite(b[2 * q + 1]))
+      return fail(h, SQ_ERR_CUDA, "per-node Lanczos bounds are not finite");
+    lo = std::min(lo, b[2 * q]);
+    hi = std::max(hi, b[2 * q + 1]);
+  }
+  h->lam_lo = lo;
+  h->lam_hi = hi;
+  return SQ_OK;
+}
+
+int run_lanczos_nodes(sq_handle* h) {
+  if (h->lanczos_k + 1 > kMaxLanczosVecs) return fail(h, SQ_ERR_INVALID_ARG, "lanczos_k too large");
+  if (h->precision == SQ_MIXED) return run_lanczos_nodes_t<float>(h);
+  return run_lanczos_nodes_t<double>(h);
 }
 
 int run_lanczos(sq_handle* h) {

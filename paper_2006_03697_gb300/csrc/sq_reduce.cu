@@ -7,6 +7,9 @@
 // rule for the Clenshaw-Curtis coefficient integral of Sec. 4; bisection on N(mu) = N_e.
 // The contraction evaluates c^j, d^j (coefficients of r g(r), App. A) and s^j (entropy
 // function) at mu and forms rho_q, E_band, E_s, E_nl and sigma (Sec. 4 stress sums).
+#include <algorithm>
+#include <cmath>
+
 #include "sq_device.cuh"
 
 namespace sq {
@@ -198,5 +201,166 @@ int run_contraction(sq_handle* h, double mu, double* rho_dev, double* out_host) 
   return SQ_OK;
 }
 
+
+// ---------------------------------------------------------------- per-node bounds mode
+// Every node q has its own interval (chi_q, zeta_q) and so its own coefficients
+// c_q^j(mu) = (2/M) sum_k g((chi_q + zeta_q cos theta_k - mu)/kT) cos(j theta_k), and
+//   N(mu) = 2 sum_q sum'_j c_q^j rho_q^j = (4/M) sum_q sum_k g(...) F_q(k),
+//   F_q(k) = sum'_j cos(j theta_k) rho_q^j      (one table of N_d x M, formed once per search).
+// tab[t] = cos(pi t / (2 M)), so cos(j theta_k) = tab[j (2 k + 1) mod 4 M].
+
+__global__ void k_cosF_nodes(const double* __restrict__ mom, int Nd, int n_pl, int M, const double* __restrict__ tab,
+                             double* __restrict__ F) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+  if (k >= M || q >= Nd) return;
+  const double* m = mom + (size_t)q * (n_pl + 1) * SQ_N_MOMENTS;
+  const long long twoM4 = 4LL * M, odd = 2LL * k + 1;
+  double s = 0.5 * m[0];
+  for (int j = 1; j <= n_pl; ++j) s += tab[(j * odd) % twoM4] * m[(size_t)j * SQ_N_MOMENTS];
+  F[(size_t)q * M + k] = s;
+}
+
+// part[block] = (4/M) sum over the block's nodes and all k of g((chi_q + zeta_q cos theta_k - mu)/kT) F_q(k)
+__global__ void k_count_nodes(const double* __restrict__ F, const double* __restrict__ nbnd, int Nd, int M,
+                              const double* __restrict__ tab, double kT, double mu, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int q = blockIdx.x; q < Nd; q += gridDim.x) {
+    const double lo = nbnd[2 * q], hi = nbnd[2 * q + 1];
+    const double chi_q = 0.5 * (hi + lo), zeta_q = 0.5 * (hi - lo);
+    const double* Fq = F + (size_t)q * M;
+    for (int k = threadIdx.x; k < M; k += blockDim.x)
+      acc += fermi_occ((chi_q + zeta_q * tab[2 * k + 1] - mu) / kT) * Fq[k];
+  }
+  const double t = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = 4.0 / M * t;
+}
+
+// out[0] = sum of part[0..n) in order; with ext: out[1] = min lo_q, out[2] = max hi_q
+__global__ void k_sum_parts(const double* __restrict__ part, int n, const double* __restrict__ nbnd, int Nd,
+                            double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < n; ++i) t += part[i];
+  out[0] = t;
+  if (nbnd) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int q = 0; q < Nd; ++q) {
+      lo = fmin(lo, nbnd[2 * q]);
+      hi = fmax(hi, nbnd[2 * q + 1]);
+    }
+    out[1] = lo;
+    out[2] = hi;
+  }
+}
+
+constexpr int kCountBlocks = 1024;
+
+int run_fermi_nodes(sq_handle* h, double* mu_out) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  const int M = h->M;
+  k_cosF_nodes<<<dim3((M + 255) / 256, h->Nd), 256, 0, s>>>(h->d.mom, h->Nd, g.n_pl, M, h->d.costab, h->d.nF);
+  SQ_LAUNCH_CHECK(h);
+  double* out = h->d.scal + 40;   // [count, min lo, max hi]
+  auto count = [&](double mu, double* res, bool ext) -> int {
+    k_count_nodes<<<kCountBlocks, 256, 0, s>>>(h->d.nF, h->d.nbnd, h->Nd, M, h->d.costab, h->kT, mu, h->d.npart);
+    SQ_LAUNCH_CHECK(h);
+    k_sum_parts<<<1, 32, 0, s>>>(h->d.npart, kCountBlocks, ext ? h->d.nbnd : nullptr, h->Nd, out);
+    SQ_LAUNCH_CHECK(h);
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(res, out, (ext ? 3 : 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+    return SQ_OK;
+  };
+  // the shared mode's rule on [min lo_q - 40 kT, max hi_q + 40 kT]
+  double e[3];
+  int rc = count(0.0, e, true);
+  if (rc != SQ_OK) return rc;
+  double lo = e[1] - 40.0 * h->kT, hi = e[2] + 40.0 * h->kT, nlo = 0.0, nhi = 0.0;
+  if ((rc = count(lo, &nlo, false)) != SQ_OK || (rc = count(hi, &nhi, false)) != SQ_OK) return rc;
+  if (!(nlo < h->n_e && h->n_e < nhi))
+    return fail(h, SQ_ERR_NO_BRACKET, "N(mu) - N_e has no sign change on the bisection bracket");
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    double nm = 0.0;
+    if ((rc = count(mid, &nm, false)) != SQ_OK) return rc;
+    if (nm < h->n_e) lo = mid;
+    else hi = mid;
+    if (hi - lo < 1e-13 * std::max(1.0, std::fabs(mid))) break;
+  }
+  if (mu_out) *mu_out = 0.5 * (lo + hi);
+  return SQ_OK;
+}
+
+// One block per node: its coefficients c, d, s at mu (M-point Chebyshev-Gauss rule, as k_coef)
+// and its contraction terms (the per-node rows of k_contract's partial sums), rho_q.
+__global__ void k_contract_nodes(const double* __restrict__ mom, const double* __restrict__ nbnd,
+                                 const double* __restrict__ v, int Nd, int n_pl, int M, const double* __restrict__ tab,
+                                 double kT, double mu, double dV, double* __restrict__ rho, double* __restrict__ rows) {
+  extern __shared__ double sm[];
+  double* fv = sm;                       // [3][M]
+  double* cf = sm + 3 * (size_t)M;       // [3][n_pl + 1]
+  const int q = blockIdx.x;
+  const double lo = nbnd[2 * q], hi = nbnd[2 * q + 1];
+  const double chi_q = 0.5 * (hi + lo), zeta_q = 0.5 * (hi - lo);
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const double r = tab[2 * k + 1];
+    const double x = (chi_q + zeta_q * r - mu) / kT;
+    const double gx = fermi_occ(x);
+    const double ax = fabs(x), ex = exp(-ax);
+    fv[k] = gx;
+    fv[M + k] = r * gx;
+    fv[2 * M + k] = -(log1p(ex) + ax * ex / (1.0 + ex));
+  }
+  __syncthreads();
+  const long long twoM4 = 4LL * M;
+  for (int t = threadIdx.x; t < 3 * (n_pl + 1); t += blockDim.x) {
+    const int which = t / (n_pl + 1), j = t % (n_pl + 1);
+    const double* f = fv + (size_t)which * M;
+    double acc = 0.0;
+    for (int k = 0; k < M; ++k) acc += f[k] * tab[((long long)j * (2 * k + 1)) % twoM4];
+    cf[t] = 2.0 / M * acc;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double* c = cf;
+  const double* d = cf + (n_pl + 1);
+  const double* sc = cf + 2 * (n_pl + 1);
+  double loc[kNPart];
+  for (int k = 0; k < kNPart; ++k) loc[k] = 0.0;
+  double r = 0.0;
+  for (int j = 0; j <= n_pl; ++j) {
+    const double wp = (j == 0) ? 0.5 : 1.0;
+    const double* m = mom + ((size_t)q * (n_pl + 1) + j) * SQ_N_MOMENTS;
+    const double cj = wp * c[j];
+    r += cj * m[0];
+    loc[0] += wp * (chi_q * c[j] + zeta_q * d[j]) * m[0];
+    loc[1] += wp * sc[j] * m[0];
+    loc[2] += cj * m[7];
+    for (int k = 0; k < 6; ++k) loc[3 + k] += cj * m[1 + k];
+    for (int k = 0; k < 9; ++k) loc[9 + k] += cj * m[8 + k];
+  }
+  if (rho) rho[q] = 2.0 / dV * r;
+  loc[18] = r;
+  loc[19] = v[q] * r;
+  for (int k = 0; k < kNPart; ++k) rows[(size_t)q * kNPart + k] = loc[k];
+}
+
+int run_contraction_nodes(sq_handle* h, double mu, double* rho_dev, double* out_host) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  const size_t smem = sizeof(double) * (3 * size_t(h->M) + 3 * size_t(g.n_pl + 1));
+  SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_contract_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  k_contract_nodes<<<h->Nd, 256, smem, s>>>(h->d.mom, h->d.nbnd, h->d.v64, h->Nd, g.n_pl, h->M, h->d.costab, h->kT,
+                                            mu, g.dV, rho_dev, h->d.nrow);
+  SQ_LAUNCH_CHECK(h);
+  k_contract_final<<<1, 32, 0, s>>>(h->d.nrow, h->Nd, h->kT, h->vol, h->d.scal);
+  SQ_LAUNCH_CHECK(h);
+  if (out_host) {
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(out_host, h->d.scal + 16, 15 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
+  return SQ_OK;
+}
 
 }  // namespace sq

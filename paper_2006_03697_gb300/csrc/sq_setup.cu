@@ -428,6 +428,30 @@ int build_tables(sq_handle* h) {
   return SQ_OK;
 }
 
+// cos(pi t / (2 M)) for t in [0, 4 M): cos(j theta_k) = tab[j (2 k + 1) mod 4 M], theta_k = pi (k + 1/2) / M
+__global__ void k_costab(int M, double* __restrict__ tab) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 4 * M) tab[t] = cos(M_PI * double(t) / (2.0 * M));
+}
+
+// neutral node intervals (0, 1) and zero step coefficients until the per-node Lanczos runs
+__global__ void k_node_init(int Nd, double* __restrict__ nbnd, double* __restrict__ ncoef) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Nd) return;
+  nbnd[2 * q] = 0.0;
+  nbnd[2 * q + 1] = 1.0;
+  ncoef[2 * q] = 0.0;
+  ncoef[2 * q + 1] = 0.0;
+}
+
+int init_node_tables(sq_handle* h) {
+  k_costab<<<(4 * h->M + 255) / 256, 256, 0, h->stream>>>(h->M, h->d.costab);
+  SQ_LAUNCH_CHECK(h);
+  k_node_init<<<(h->Nd + 255) / 256, 256, 0, h->stream>>>(h->Nd, h->d.nbnd, h->d.ncoef);
+  SQ_LAUNCH_CHECK(h);
+  return SQ_OK;
+}
+
 int build_wave_lists(sq_handle* h, const Wave& w) {
   if (h->precision == SQ_FP64)
     return wave_lists_t<double>(h, w, h->d.chi64, h->d.gdv64, (double*)h->wb.A, (double*)h->wb.W, (double*)h->wb.T[0]);

@@ -205,13 +205,13 @@ static int step_warps(int bricks_per_slab) {
 }
 
 template <typename Real, int NO, bool kSmemP, bool kMMA>
-__global__ void __launch_bounds__(kStepThreads, sizeof(Real) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kStepThreads, sizeof(Real) == 4 ? 4 : 2)
 k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, Real* __restrict__ Tn,
        const double* __restrict__ Pg, double* __restrict__ Pg_next, const Real* __restrict__ Wt,
        const Real* __restrict__ chi, const float* __restrict__ chis, const Real* __restrict__ gdv,
        const int4* __restrict__ brec, const int* __restrict__ slab_n, const int* __restrict__ slab_map, const int* __restrict__ bn,
        const Real* __restrict__ v, const double* __restrict__ scal, int mode, double* __restrict__ Spart,
-       int rows_smem) {
+       int rows_smem, const double* __restrict__ ncoef) {
   // dynamic shared memory: [Ps: rows_smem x 8 FP64][red: nw x 8 x 9 FP64][Pstage: rows_smem x 8]
   // [tn_sm: nw x 16 x 32] (Ps and Pstage only with kSmemP; rows_smem = 0 otherwise)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -268,6 +268,25 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   qo[1] = (q >> 1) & 1;
   qo[2] = q >> 2;
   const bool valid = node_valid(g, o, qo);
+  // step coefficients of the lane's node(s): the block's (shared bounds) or each node's own
+  // (per-node bounds; paired phase: nodes 2 np2 and 2 np2 + 1, scalar phase: node q)
+  Real caA = ca, cdA = cd, caB = ca, cdB = cd;
+  if (ncoef) {
+    auto own = [&](int qx, int qy, int qz, Real& c_a, Real& c_d) {
+      const int qq[3] = {qx, qy, qz};
+      if (!node_valid(g, o, qq)) return;
+      const int node = (o[0] + qx) + g.n[0] * ((o[1] + qy) + g.n[1] * (o[2] + qz));
+      c_a = Real(f * ncoef[2 * node]);
+      c_d = Real(f * ncoef[2 * node + 1]);
+    };
+    if constexpr (kMMA) {
+      const int p2 = lane & 3;
+      own(0, p2 & 1, p2 >> 1, caA, cdA);
+      own(1, p2 & 1, p2 >> 1, caB, cdB);
+    } else {
+      own(qo[0], qo[1], qo[2], caA, cdA);
+    }
+  }
   const Real* Wq = Wt + (size_t)tl * 3 * g.Upts * kTileB;
   const size_t wstr = (size_t)g.Upts * kTileB;
   // S partial sums: per lane across bricks (scalar path); the paired phase B reduces them per
@@ -427,9 +446,9 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
           y.x += ynl.x;
           y.y += ynl.y;
           if (mode != 2) {
-            const float dg = float(cd) + float(ca) * vloc;
-            if (in0) tn.x = float(ca) * y.x + dg * tc.x - float(cc) * tp.x;
-            if (in1) tn.y = float(ca) * y.y + dg * tc.y - float(cc) * tp.y;
+            const float dgA = float(cdA) + float(caA) * vloc, dgB = float(cdB) + float(caB) * vloc;
+            if (in0) tn.x = float(caA) * y.x + dgA * tc.x - float(cc) * tp.x;
+            if (in1) tn.y = float(caB) * y.y + dgB * tc.y - float(cc) * tp.y;
             *reinterpret_cast<float2*>(Tn + tbase + e) = tn;
           }
 #pragma unroll
@@ -486,7 +505,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
           const Real vloc = v[wrz[uz] + wry[pb] + wrx[ux]];   // V_eff at the wrapped node
           y += tnv[it * 32];                          // nonlocal part from phase A
           if (mode != 2) {
-            tn = ca * y + (cd + ca * vloc) * tc - cc * tp;
+            tn = caA * y + (cdA + caA * vloc) * tc - cc * tp;
             Tn[tbase + e] = tn;
           }
 #pragma unroll
@@ -703,6 +722,7 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
                        const double* Pg, double* Pgn, const Real* W, const Real* chi, const Real* gdv, const Real* v,
                        int mode) {
   const int rows_smem = int(smem / (kTileB * (sizeof(double) + sizeof(Real))));
+  const double* ncoef = (h->bounds_mode == SQ_BOUNDS_PER_NODE) ? h->d.ncoef : nullptr;
   const int nw = step_warps(h->geo.nbr[0] * h->geo.nbr[2]), nthr = 32 * nw;
   const size_t smem_warps = size_t(nw) * (kTileB * 9 * sizeof(double) + 16 * 32 * sizeof(Real));
   // The dynamic-size attribute belongs to the function, not the launch, and handles on other
@@ -716,7 +736,7 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmemMax));
       k_step<Real, NO, true, sizeof(Real) == 4><<<grid, nthr, smem, h->stream>>>(
           h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.chi32s, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n,
-          v, h->d.scal, mode, h->wb.Spart, rows_smem);
+          v, h->d.scal, mode, h->wb.Spart, rows_smem, ncoef);
       SQ_LAUNCH_CHECK(h);
       return SQ_OK;
     }
@@ -725,14 +745,14 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
                                         kStepSmemMax));
     k_step<Real, NO, true, false><<<grid, nthr, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
                                                                 h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
-                                                                h->d.scal, mode, h->wb.Spart, rows_smem);
+                                                                h->d.scal, mode, h->wb.Spart, rows_smem, ncoef);
   } else {
     h->step_variant[2]++;
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
     k_step<Real, NO, false, false><<<grid, nthr, smem_warps, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
                                                               h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
-                                                              h->d.scal, mode, h->wb.Spart, 0);
+                                                              h->d.scal, mode, h->wb.Spart, 0, ncoef);
   }
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;

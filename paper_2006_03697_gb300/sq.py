@@ -24,13 +24,15 @@ SQ_FP64 = 0
 SQ_MIXED = 1
 SQ_BOUNDS_LANCZOS = 0
 SQ_BOUNDS_GIVEN = 1
+SQ_BOUNDS_PER_NODE = 2
 SQ_N_MOMENTS = 17
 
 EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_node_sums", "sq_fermi_level_sums",
     "sq_density_energy_stress",
-    "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_moments_copy", "sq_footprint_bytes",
-    "sq_kernel_launches", "sq_step_launch_counts", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit",
+    "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_node_bounds", "sq_moments_copy", "sq_footprint_bytes",
+    "sq_kernel_launches", "sq_step_launch_counts", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit", "sq_server_submit_traj", "sq_server_resident",
+    "sq_update_atoms",
     "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_gauss_density", "sq_green_kubo", "sq_destroy",
     "sq_last_error",
 ]
@@ -95,6 +97,8 @@ def lib():
         L.sq_density_energy_stress_dev.argtypes = [H, C.c_double, C.c_void_p, C.POINTER(sq_energies), C.c_void_p]
         L.sq_pressure.argtypes = [H, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.sq_get_bounds.argtypes = [H, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.sq_node_bounds.argtypes = [H, C.c_void_p, C.c_void_p]
+        L.sq_node_bounds.restype = C.c_int
         L.sq_moments_copy.argtypes = [H, C.c_void_p]
         L.sq_footprint_bytes.argtypes = [C.POINTER(sq_instance_desc)]
         L.sq_footprint_bytes.restype = C.c_size_t
@@ -116,6 +120,12 @@ def lib():
         L.sq_server_create.restype = C.c_int
         L.sq_server_submit.argtypes = [C.c_void_p, C.POINTER(sq_instance_desc), C.c_longlong]
         L.sq_server_submit.restype = C.c_int
+        L.sq_server_submit_traj.argtypes = [C.c_void_p, C.POINTER(sq_instance_desc), C.c_longlong, C.c_longlong]
+        L.sq_server_submit_traj.restype = C.c_int
+        L.sq_server_resident.argtypes = [C.c_void_p]
+        L.sq_server_resident.restype = C.c_int
+        L.sq_update_atoms.argtypes = [H, C.c_void_p, C.c_void_p]
+        L.sq_update_atoms.restype = C.c_int
         L.sq_server_poll.argtypes = [C.c_void_p, C.POINTER(sq_result), C.c_int, C.c_int, C.POINTER(C.c_int)]
         L.sq_server_poll.restype = C.c_int
         L.sq_server_pending.argtypes = [C.c_void_p]
@@ -132,7 +142,7 @@ def lib():
         L.sq_last_error.argtypes = [H]
         L.sq_last_error.restype = C.c_char_p
         for name in ("sq_setup", "sq_moments", "sq_fermi_level", "sq_density_energy_stress",
-                     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_moments_copy"):
+                     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_node_bounds", "sq_moments_copy"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -173,6 +183,10 @@ class Desc:
         d.precision = int(precision)
         if bounds is None:
             d.bounds_mode = SQ_BOUNDS_LANCZOS
+        elif isinstance(bounds, str):
+            if bounds != "per_node":
+                raise ValueError(f"unknown bounds mode {bounds!r}")
+            d.bounds_mode = SQ_BOUNDS_PER_NODE
         else:
             d.bounds_mode = SQ_BOUNDS_GIVEN
             d.lambda_lo, d.lambda_hi = float(bounds[0]), float(bounds[1])
@@ -204,6 +218,13 @@ def sq_fermi_level(h) -> float:
     mu = C.c_double()
     _check(lib().sq_fermi_level(h, C.byref(mu)), h)
     return mu.value
+
+
+def sq_update_atoms(h, pos, v_eff):
+    """New atom positions [n_atoms][3] and V_eff [N_d] for a live handle (same cell and species)."""
+    pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+    v = np.ascontiguousarray(v_eff, dtype=np.float64)
+    _check(lib().sq_update_atoms(h, pos.ctypes.data if pos.size else None, v.ctypes.data), h)
 
 
 def sq_node_sums(h, n_pl: int) -> np.ndarray:
@@ -312,6 +333,13 @@ def sq_get_bounds(h):
     return lo.value, hi.value
 
 
+def sq_node_bounds(h, nd: int):
+    """Per-node effective intervals (lo, hi), each (N_d,), in SQ_BOUNDS_PER_NODE mode."""
+    lo, hi = np.zeros(nd), np.zeros(nd)
+    _check(lib().sq_node_bounds(h, lo.ctypes.data, hi.ctypes.data), h)
+    return lo, hi
+
+
 def sq_moments_copy(h, nd: int, n_pl: int):
     out = np.zeros((nd, n_pl + 1, SQ_N_MOMENTS))
     _check(lib().sq_moments_copy(h, out.ctypes.data), h)
@@ -380,6 +408,8 @@ def run(inst: dict, precision=SQ_FP64, bounds=None, want_moments=False, stream=N
         out.update(en)
         if want_moments:
             out["moments"] = sq_moments_copy(h, nd, int(inst["n_pl"]))
+        if isinstance(bounds, str):
+            out["node_bounds"] = sq_node_bounds(h, nd)
         return out
     finally:
         sq_destroy(h)
@@ -428,10 +458,16 @@ class Server:
         self.h = C.c_void_p()
         _check(lib().sq_server_create(int(hbm_budget_bytes), int(max_inflight), C.byref(self.h)))
 
-    def submit(self, desc: Desc, tag: int):
-        rc = lib().sq_server_submit(self.h, C.byref(desc.c), int(tag))
+    def submit(self, desc: Desc, tag: int, traj: int | None = None):
+        if traj is None:
+            rc = lib().sq_server_submit(self.h, C.byref(desc.c), int(tag))
+        else:
+            rc = lib().sq_server_submit_traj(self.h, C.byref(desc.c), int(tag), int(traj))
         if rc != SQ_OK:
             raise SQError(rc, "sq_server_submit rejected the request")
+
+    def resident(self) -> int:
+        return int(lib().sq_server_resident(self.h))
 
     def poll(self, max_results: int = 64, timeout_ms: int = 100):
         buf = (sq_result * max_results)()
