@@ -56,8 +56,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests in the served-stream measurement (0 disables it)")
     ap.add_argument("--serve-trajectories", type=int, default=8)
-    ap.add_argument("--batch", type=int, default=6,
+    ap.add_argument("--batch", type=int, default=8,
                     help="instances in the batched-snapshot measurement (0 disables it)")
+    ap.add_argument("--no-large", dest="large", action="store_false",
+                    help="skip the largest single-GPU configurations (216 H / 60^3, 512 H / 80^3)")
     ap.add_argument("--profile-case", action="store_true",
                     help="only run two sweeps of the small profiling case (16^3 cell at the 40^3 "
                          "workload's parameters and atom density) for a profiler capture; prints no bench line")
@@ -298,35 +300,78 @@ def serve_stream(sq, n_req: int, prec: int, n_traj: int = 8, max_inflight: int =
                         "setup included) sets the rate and is not in the latency statistics"}
 
 
-def batch_throughput(sq, prec: int, count: int = 6, concurrent: int = 3):
-    """A batch of uneven snapshots of the batched workload (32 / 64 / 128-atom cells with their
-    own grid, kT, n_pl and R_cut) evaluated together by sq_batch_evaluate (each on its own stream,
-    `concurrent` at a time): evaluations/s and region point-steps/s of the whole batch."""
+def batch_throughput(sq, prec: int, count: int = 8):
+    """Uneven snapshots of the batched workload (32 ... 512-atom cells with their own grid, kT,
+    n_pl and R_cut; one 256- and one 512-atom cell among them) evaluated by ONE CUDA graph
+    (sq_batch_create captures every member's Lanczos bounds, sweep, Fermi level and
+    contraction as a branch; sq_batch_run launches it): evaluations/s and region point-steps/s
+    of the whole batch, timed on the second launch (the first one warms up)."""
     import numpy as np
     import torch
     from workloads import make_batch
-    insts = make_batch(config=4, count=count, atom_choices=(32, 64, 128))
+    insts = make_batch(config=4, count=max(2, count - 2), atom_choices=(32, 64, 128))
+    insts += make_batch(config=4, count=1, start=200, atom_choices=(256,))
+    insts += make_batch(config=4, count=1, start=201, atom_choices=(512,))
     streams = [torch.cuda.Stream() for _ in insts]
     hs = [sq.sq_setup(sq.Desc(inst, prec, bounds=None, stream=st.cuda_stream)) for inst, st in zip(insts, streams)]
     point_steps = 0.0
     for inst in insts:
         m = np.floor(float(inst["r_cut"]) / (np.asarray(inst["L"]) / np.asarray(inst["n"])) + 1e-9)
         point_steps += float(np.prod(inst["n"])) * float(np.prod(2 * m + 1)) * float(inst["n_pl"])
+    batch = None
     try:
+        batch = sq.Batch(hs)
+        batch.run()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        mu, en, sig = sq.sq_batch_evaluate(hs, max_concurrent=concurrent)
-        torch.cuda.synchronize()
+        mu, en, sig = batch.run()
         wall = time.perf_counter() - t0
     finally:
+        if batch is not None:
+            batch.close()
         for h in hs:
             sq.sq_destroy(h)
-    return {"instances": count, "concurrent": concurrent, "evals_per_s": count / wall, "wall_s": wall,
+    return {"instances": len(insts), "graph_launches_timed": 1, "evals_per_s": len(insts) / wall, "wall_s": wall,
             "point_steps_per_s": point_steps / wall,
             "atoms": [int(len(i["pos"])) for i in insts], "n_pl": [int(i["n_pl"]) for i in insts],
             "ok": bool(all(abs(e["N_check"] - i["n_e"]) <= 1e-8 * i["n_e"] for e, i in zip(en, insts))),
-            "workload": "uneven snapshots of the batched config (32/64/128 H at 0.0375 / bohr^3, h = 0.3, "
-                        "kT in [1.6, 6.3], n_pl in [30, 80], R_cut in [3, 5]), device Lanczos bounds"}
+            "workload": "uneven snapshots of the batched config (32-512 H at 0.0375 / bohr^3, h = 0.3, kT in "
+                        "[1.6, 6.3], n_pl in [30, 80], R_cut in [3, 5]), device Lanczos bounds, one CUDA graph"}
+
+
+def large_configs(sq, prec: int):
+    """The largest single-GPU workloads, one warm-up and one timed evaluation each (setup outside,
+    device Lanczos bounds inside the timed evaluation): 216 H in an 18 bohr cube (60^3 nodes,
+    27^3 regions, n_pl = 60) and the largest batched snapshot (512 H, 80^3 nodes)."""
+    import numpy as np
+    import torch
+    from workloads import make_batch, make_instance
+    out = {}
+    cases = (("216H_18bohr_60cube_no6_sp_rcut4_npl60", make_instance(3)),
+             ("512H_24bohr_80cube_batched_snapshot", make_batch(4, count=1, atom_choices=(512,))[0]))
+    for name, inst in cases:
+        st = torch.cuda.Stream()
+        h = sq.sq_setup(sq.Desc(inst, prec, bounds=None, stream=st.cuda_stream))
+        nd = int(np.prod(inst["n"]))
+        try:
+            def ev():
+                sq.sq_moments(h)
+                mu = sq.sq_fermi_level(h)
+                return sq.sq_density_energy_stress(h, mu, None)
+            ev()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, en, _ = ev()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        finally:
+            sq.sq_destroy(h)
+        m = np.floor(float(inst["r_cut"]) / (np.asarray(inst["L"]) / np.asarray(inst["n"])) + 1e-9)
+        ps = float(nd) * float(np.prod(2 * m + 1)) * float(inst["n_pl"])
+        out[name] = {"s_per_eval": dt, "evals_per_s": 1.0 / dt, "point_steps_per_s": ps / dt,
+                     "nodes": nd, "region": [int(2 * x + 1) for x in m], "n_pl": int(inst["n_pl"]),
+                     "N_check": en["N_check"], "n_e": float(inst["n_e"])}
+    return out
 
 
 def run_reference(args):
@@ -440,7 +485,11 @@ def run_ours(args):
         en = sq.sq_density_energy_stress_dev(h, mu, rho_dev.data_ptr(), sig_dev.data_ptr(), energies=True)
         return finish(h, mu, en)
 
-    for _ in range(args.warmup):
+    en = step()
+    # autotuner: warps per step block and tiles per wave for this geometry (cached per shape),
+    # chosen before the warm-up and the timed region
+    tune_key, tune_choice, _ = sq.autotune_step(h, inst, prec)
+    for _ in range(max(0, args.warmup - 1)):
         en = step()
     torch.cuda.synchronize()
     if dist:
@@ -518,6 +567,7 @@ def run_ours(args):
                    "node_columns_per_step": nd,
                    "flush_l2": f"no flush: device working set {sq.sq_footprint_bytes(desc) / 1e9:.1f} GB > L2"},
         "node_columns_per_s": value * nd,
+        "autotune": {"key": tune_key, **tune_choice},
         "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
         "kernels": kern, "energies": {k: en[k] for k in ("E_band", "E_s", "E_nl", "F", "N_check", "mu")},
         "sigma": sig_dev.cpu().numpy().reshape(3, 3).tolist(),
@@ -556,8 +606,13 @@ def run_ours(args):
     sq.sq_destroy(h)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         line["serving"] = serve_stream(sq, args.serve_requests, prec, n_traj=args.serve_trajectories)
+    if rank == 0 and world == 1 and args.large:
+        line["large_configs"] = large_configs(sq, prec)
     if rank == 0 and world == 1 and args.batch > 0:
         line["batch"] = batch_throughput(sq, prec, count=args.batch)
+        m = np.floor(float(inst["r_cut"]) / (np.asarray(inst["L"]) / np.asarray(inst["n"])) + 1e-9)
+        line["batch"]["single_instance_point_steps_per_s"] = (float(nd) * float(np.prod(2 * m + 1)) *
+                                                              float(inst["n_pl"]) * value)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(inst, args.cpu_nodes)
     if rank == 0:

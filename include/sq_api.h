@@ -225,6 +225,16 @@ long long sq_kernel_launches(const sq_handle* h);
  * which a block uses global memory (tuning and tests). Errors: SQ_ERR_INVALID_ARG. */
 int sq_step_launch_counts(const sq_handle* h, long long* counts);
 
+/* Autotuning hook of the step kernel: n_warps warps per step block (1..8; 0 = the default,
+ * the count that leaves the fewest idle warps over a slab's bricks) and at most wave_tiles tiles
+ * per launch (0 = as many as the buffers sized at sq_setup hold; waves are spread evenly over the
+ * handle's tiles). The settings stay with the handle. With reps > 0 and ms_per_tile non-NULL,
+ * also times reps recurrence-step launches of the first wave with CUDA events on the handle's
+ * stream and returns milliseconds per tile and step (needs the bounds: after sq_moments, or
+ * SQ_BOUNDS_GIVEN; the sweep buffers are reused, the moments table is not touched).
+ * Synchronises. Errors: SQ_ERR_INVALID_ARG, SQ_ERR_STATE, SQ_ERR_CUDA. */
+int sq_tune_step(sq_handle* h, int n_warps, int wave_tiles, int reps, double* ms_per_tile);
+
 /* Kernel classes of the Chebyshev sweep timed by sq_kernel_timing (see below). */
 #define SQ_K_STENCIL 0   /* H t^j, window mask, recurrence update, S partials          */
 #define SQ_K_PROJECT 1   /* chi^T t^{j+1} per atom image                                */
@@ -273,6 +283,24 @@ int sq_fermi_level_noalloc(const double* mom_dev, int n_nodes, int n_pl, double 
  * Returns the first non-zero status (details in that handle's sq_last_error). */
 int sq_batch_evaluate(sq_handle* const* hs, int n, int max_concurrent, double* mu_out, sq_energies* e_out,
                       double* sigma_out);
+
+/* One CUDA graph for a batch of handles (uneven instances: atom counts, cells, R_cut, n_pl,
+ * precisions may differ; SQ_BOUNDS_LANCZOS or SQ_BOUNDS_GIVEN): sq_batch_create captures each
+ * member's whole evaluation (Lanczos bounds, sweep with moments, Fermi level, contraction) as
+ * one branch of the graph, with nothing crossing to the host inside it; sq_batch_run launches
+ * the graph once, waits, and writes the members' results (host, may be NULL): mu_out [n],
+ * e_out [n], sigma_out [n][9]; the members' moments and density (sq_moments_copy,
+ * sq_density_energy_stress at another mu) are then available as after sq_moments. Members need
+ * their own non-NULL streams and must not be used elsewhere while the batch runs. After
+ * sq_update_atoms on members, sq_batch_run evaluates the new snapshots (re-capturing the graph
+ * when a member's wave layout grew). Errors: SQ_ERR_INVALID_ARG (NULL, repeated handles or
+ * streams, per-node bounds), SQ_ERR_CUDA, SQ_ERR_NO_BRACKET (first failing member; its handle's
+ * sq_last_error, sq_batch_last_error says which). */
+typedef struct sq_batch sq_batch;
+int sq_batch_create(sq_handle* const* hs, int n, sq_batch** out);
+int sq_batch_run(sq_batch* b, double* mu_out, sq_energies* e_out, double* sigma_out);
+const char* sq_batch_last_error(const sq_batch* b);
+void sq_batch_destroy(sq_batch* b);
 
 /* Request loop with continuous batching (one GPU). Requests are admitted in submission order
  * as soon as their device footprint (sq_footprint_bytes) fits under hbm_budget_bytes next to

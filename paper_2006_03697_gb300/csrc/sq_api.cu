@@ -350,37 +350,15 @@ int fail(sq_handle* h, int code, const std::string& msg) {
   return code;
 }
 
+// Given bounds go through the same device scaling as the Lanczos ones (set_bounds_device):
+// the FP32-exact coefficients of SQ_MIXED, one rounding of the diagonal coefficient, and the
+// effective interval the recurrence realises.
 int set_bounds(sq_handle* h, double lo, double hi) {
-  double chi = 0.5 * (hi + lo), zeta = 0.5 * (hi - lo);
-  double ca = 2.0 / zeta, cb = -2.0 * chi / zeta;
-  if (h->precision == SQ_MIXED) {
-    // FP32 step coefficients, and the half-width / centre they realise exactly
-    ca = double(float(ca));
-    zeta = 2.0 / ca;
-    cb = double(float(-2.0 * chi / zeta));
-    chi = -cb * zeta / 2.0;
-  }
-  // The sweep multiplies t by one diagonal coefficient cd = ca lap0 + cb (plus ca V), formed
-  // here in FP64 so the large, nearly cancelling diagonal terms never meet in FP32; its
-  // rounding eps to the sweep precision acts as a constant shift eps / ca of the operator.
-  double cd = ca * h->geo.lap0 + cb;
-  if (h->precision == SQ_MIXED) cd = double(float(cd));
-  const double eps = cd - (ca * h->geo.lap0 + cb);
-  // the stored stencil adds (lap_offset + eps / ca) t: the recurrence runs on
-  // (H + offset - chi) / zeta, so the effective centre moves down by that offset
-  chi -= h->lap_offset + eps / ca;
-  h->lam_lo = chi - zeta;
-  h->lam_hi = chi + zeta;
-  h->hscal[0] = h->lam_lo;
-  h->hscal[1] = h->lam_hi;
-  h->hscal[2] = ca;
-  h->hscal[3] = cb;
-  h->hscal[4] = cd;
-  cudaError_t e = cudaMemcpyAsync(h->d.scal, h->hscal, 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->d.scal + 4, h->hscal + 2, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  h->hscal[0] = lo;
+  h->hscal[1] = hi;
+  cudaError_t e = cudaMemcpyAsync(h->d.scal + 8, h->hscal, 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return fail(h, SQ_ERR_CUDA, std::string("set_bounds: ") + cudaGetErrorString(e));
-  return SQ_OK;
+  return set_bounds_device(h);
 }
 
 cudaEvent_t timing_begin(sq_handle* h, int kid, double bytes) {
@@ -635,6 +613,8 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
     rc = sq::init_node_tables(h);
     if (rc != SQ_OK) return cleanup(rc);
   }
+  rc = sq::measure_wave_rows(h);   // the sweep then needs no host round trip
+  if (rc != SQ_OK) return cleanup(rc);
 
   *out = h;
   return SQ_OK;
@@ -691,7 +671,9 @@ int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff) {
     SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.lz_tiles, lz.data(), sizeof(int) * lz.size(), cudaMemcpyHostToDevice, s));
     h->bounds_ready = false;
   }
-  const int rc = sq::build_tables(h);
+  int rc = sq::build_tables(h);
+  if (rc != SQ_OK) return rc;
+  rc = sq::measure_wave_rows(h);   // the atoms moved: the slabs meet other projector rows
   if (rc != SQ_OK) return rc;
   // pageable host sources: the copies have read them before the call returns; the handle's
   // results now describe the new snapshot only after the next sq_moments
@@ -775,8 +757,23 @@ int sq_pressure(sq_handle* h, double mu, double* pressure_out, double* e_pot_out
 int sq_get_bounds(const sq_handle* h, double* lo, double* hi) {
   if (!h || !lo || !hi) return SQ_ERR_INVALID_ARG;
   if (!h->bounds_ready) return SQ_ERR_STATE;
-  *lo = h->lam_lo;
-  *hi = h->lam_hi;
+  if (h->bounds_mode == SQ_BOUNDS_PER_NODE) {
+    *lo = h->lam_lo;
+    *hi = h->lam_hi;
+    return SQ_OK;
+  }
+  // the effective interval lives on the device (scaled there, from the Lanczos or given bounds)
+  double b[2];
+  int st[sq::kStCount];
+  if (cudaMemcpyAsync(b, h->d.scal, sizeof(b), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(st, h->d.status, sizeof(st), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return SQ_ERR_CUDA;
+  }
+  if (st[sq::kStBadBounds]) return SQ_ERR_CUDA;
+  *lo = b[0];
+  *hi = b[1];
   return SQ_OK;
 }
 
@@ -804,6 +801,30 @@ int sq_moments_copy(sq_handle* h, double* host_out) {
 }
 
 long long sq_kernel_launches(const sq_handle* h) { return h ? h->launches : 0; }
+
+int sq_tune_step(sq_handle* h, int n_warps, int wave_tiles, int reps, double* ms_per_tile) {
+  if (!h || n_warps < 0 || n_warps > 8 || wave_tiles < 0 || reps < 0) return SQ_ERR_INVALID_ARG;
+  h->step_warps = n_warps;
+  // new wave split over the handle's tiles, within the buffers sized at setup, evenly spread
+  const int ntl = h->tile_end - h->tile_begin;
+  const int cap = (wave_tiles > 0) ? std::min(wave_tiles, h->wave_cap) : h->wave_cap;
+  const int nwaves = std::max(1, (ntl + cap - 1) / std::max(1, cap));
+  const int per = std::max(1, (ntl + nwaves - 1) / nwaves);
+  h->waves.clear();
+  for (int t0 = h->tile_begin; t0 < h->tile_end; t0 += per) h->waves.push_back({t0, std::min(per, h->tile_end - t0), nullptr});
+  h->wave_rows.clear();
+  int rc = sq::measure_wave_rows(h);
+  if (rc != SQ_OK) return rc;
+  if (reps > 0 && ms_per_tile) {
+    // the timed launches reuse the sweep buffers of wave 0; the moments table is not touched
+    if (!h->bounds_ready) return sq::fail(h, SQ_ERR_STATE, "sq_tune_step timing needs the bounds (sq_moments first)");
+    double ms = 0.0;
+    rc = sq::time_step_launch(h, reps, &ms);
+    if (rc != SQ_OK) return rc;
+    *ms_per_tile = h->waves.empty() ? 0.0 : ms / h->waves[0].ntiles;
+  }
+  return SQ_OK;
+}
 
 int sq_step_launch_counts(const sq_handle* h, long long* counts) {
   if (!h || !counts) return SQ_ERR_INVALID_ARG;

@@ -176,6 +176,7 @@ struct sq_handle {
   int n_ch_total = 0;
   bool proj4 = false;               // every atom has at most 4 projector channels (one group per image)
   std::vector<sq::Wave> waves;
+  std::vector<int> wave_rows;       // per wave: most projector rows of a slab (shared-memory size)
   int tile_begin = 0, tile_end = 0;   // tiles this handle sweeps (node partition)
   int wave_cap = 0;
   sq::Dev d;
@@ -186,6 +187,7 @@ struct sq_handle {
   // projector phases; [1] shared memory, scalar phases; [2] projections in global memory
   long long step_variant[3] = {0, 0, 0};
   int step_rows_cap = 0;            // most projector rows a step block stages in shared memory
+  int step_warps = 0;               // warps per step block (0: the brick-count rule; set by the tuner)
   // optional event timing of the sweep kernels
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -203,6 +205,13 @@ namespace sq {
 // Spectral scaling of the recurrence from bounds [lo, hi] (sq_api.cu): writes the step
 // coefficients and the effective bounds used by the Fermi search and the contraction.
 int set_bounds(sq_handle* h, double lo, double hi);
+// The same scaling on the device from the Lanczos interval in scal[8], scal[9] (sq_lanczos.cu)
+int set_bounds_device(sq_handle* h);
+// per-wave slab row counts (sq_sweep.cu): sizes the step kernel's shared memory, once per layout
+int measure_wave_rows(sq_handle* h);
+// one recurrence step launch (mode 1) of wave 0 with the handle's current settings, timed with
+// CUDA events on its stream (sq_sweep.cu; the autotuner's measurement)
+int time_step_launch(sq_handle* h, int reps, double* ms_out);
 
 // error helpers
 int fail(sq_handle* h, int code, const std::string& msg);
@@ -254,8 +263,10 @@ int run_contraction_nodes(sq_handle* h, double mu, double* rho_dev, double* sums
 int run_node_sums(sq_handle* h, double* R_out);
 int run_fermi_sums(sq_handle* h, const double* R_host, double* mu_out);
 int run_contraction(sq_handle* h, double mu, double* rho_dev, double* sums_host);
+// Fermi level + contraction with mu and the outputs kept on the device (sq_reduce.cu)
+int run_fermi_contraction_device(sq_handle* h);
 
 // status word indices
-enum StatusWord { kStOverflow = 0, kStNoBracket = 1, kStTimeout = 2, kStNoConverge = 3, kStCount = 4 };
+enum StatusWord { kStOverflow = 0, kStNoBracket = 1, kStTimeout = 2, kStNoConverge = 3, kStBadBounds = 4, kStCount = 5 };
 
 }  // namespace sq

@@ -377,12 +377,45 @@ static int run_lanczos_t(sq_handle* h) {
   cudaStream_t s = h->stream;
   k_lz_bounds<<<1, 256, 0, s>>>(ncols, k, alpha, beta, keff, h->d.scal);
   SQ_LAUNCH_CHECK(h);
-  double b2[2];
-  SQ_CUDA_TRY(h, cudaMemcpyAsync(b2, h->d.scal + 8, sizeof(b2), cudaMemcpyDeviceToHost, s));
-  SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
-  if (!(b2[0] < b2[1]) || !std::isfinite(b2[0]) || !std::isfinite(b2[1]))
-    return fail(h, SQ_ERR_CUDA, "Lanczos bounds are not finite");
-  return set_bounds(h, b2[0], b2[1]);
+  return set_bounds_device(h);   // no host round trip: the whole evaluation can be graph-captured
+}
+
+// set_bounds on the device, from the Lanczos interval scal[8], scal[9]: the step coefficients
+// ca = 2 / zeta, cb = -2 chi / zeta, cd = ca lap0 + cb (SQ_MIXED: FP32-exact ca and cb, cd rounded
+// once) and the effective interval the recurrence realises (centre moved by the stored
+// stencil's constant-mode offset and cd's rounding) in scal[0], scal[1], scal[4..6]. Explicit
+// rounding intrinsics keep every product and sum separately rounded, as in set_bounds.
+__global__ void k_set_bounds(double* __restrict__ scal, double lap0, double lap_offset, int mixed, int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double lo = scal[8], hi = scal[9];
+  if (!(lo < hi) || !isfinite(lo) || !isfinite(hi)) {
+    status[kStBadBounds] = 1;
+    return;
+  }
+  status[kStBadBounds] = 0;
+  double chi = __dmul_rn(0.5, __dadd_rn(hi, lo)), zeta = __dmul_rn(0.5, __dsub_rn(hi, lo));
+  double ca = __ddiv_rn(2.0, zeta), cb = __ddiv_rn(__dmul_rn(-2.0, chi), zeta);
+  if (mixed) {
+    ca = double(__double2float_rn(ca));
+    zeta = __ddiv_rn(2.0, ca);
+    cb = double(__double2float_rn(__ddiv_rn(__dmul_rn(-2.0, chi), zeta)));
+    chi = __ddiv_rn(__dmul_rn(-cb, zeta), 2.0);
+  }
+  const double exact = __dadd_rn(__dmul_rn(ca, lap0), cb);
+  const double cd = mixed ? double(__double2float_rn(exact)) : exact;
+  const double eps = __dsub_rn(cd, exact);
+  chi = __dsub_rn(chi, __dadd_rn(lap_offset, __ddiv_rn(eps, ca)));
+  scal[0] = __dsub_rn(chi, zeta);
+  scal[1] = __dadd_rn(chi, zeta);
+  scal[4] = ca;
+  scal[5] = cb;
+  scal[6] = cd;
+}
+
+int set_bounds_device(sq_handle* h) {
+  k_set_bounds<<<1, 32, 0, h->stream>>>(h->d.scal, h->geo.lap0, h->lap_offset, h->precision == SQ_MIXED, h->d.status);
+  SQ_LAUNCH_CHECK(h);
+  return SQ_OK;
 }
 
 // Per-node bounds: every node column of the handle's tiles, in waves of nlz_wave tiles.

@@ -156,6 +156,8 @@ static int fermi_from_R(sq_handle* h, double* mu_out) {
   SQ_CUDA_TRY(h, cudaMemcpyAsync(&mu, h->d.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
   SQ_CUDA_TRY(h, cudaMemcpyAsync(st, h->d.status, sizeof(st), cudaMemcpyDeviceToHost, s));
   SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (st[kStBadBounds]) return fail(h, SQ_ERR_CUDA, "spectral bounds are not finite or empty");
+  if (st[kStOverflow]) return fail(h, SQ_ERR_CUDA, "internal list capacity exceeded");
   if (st[kStNoBracket]) return fail(h, SQ_ERR_NO_BRACKET, "N(mu) - N_e has no sign change on the bisection bracket");
   if (mu_out) *mu_out = mu;
   return SQ_OK;
@@ -180,6 +182,32 @@ int run_fermi_sums(sq_handle* h, const double* R_host, double* mu_out) {
   SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.R, R_host, sizeof(double) * (h->geo.n_pl + 1), cudaMemcpyHostToDevice,
                                  h->stream));
   return fermi_from_R(h, mu_out);
+}
+
+__global__ void k_copy_scalar(double* __restrict__ scal, int dst, int src) { scal[dst] = scal[src]; }
+
+// The Fermi level and the contraction with nothing crossing to the host (graph capture): mu
+// stays in scal[2] (NaN and the no-bracket status word when there is no sign change), the
+// contraction takes it from there and leaves its outputs in scal[16 ..].
+int run_fermi_contraction_device(sq_handle* h) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  k_rsum<<<g.n_pl + 1, 256, 0, s>>>(h->d.mom, h->Nd, g.n_pl, h->d.R);
+  SQ_LAUNCH_CHECK(h);
+  k_cosF<<<(h->M + 255) / 256, 256, 0, s>>>(h->d.R, g.n_pl, h->M, h->d.cosF);
+  SQ_LAUNCH_CHECK(h);
+  k_bisect<<<1, 1024, 0, s>>>(h->d.cosF, h->M, h->kT, h->n_e, h->d.scal, h->d.status);
+  SQ_LAUNCH_CHECK(h);
+  k_copy_scalar<<<1, 1, 0, s>>>(h->d.scal, 3, 2);
+  SQ_LAUNCH_CHECK(h);
+  k_coef<<<3, 256, sizeof(double) * h->M, s>>>(h->d.scal, h->kT, g.n_pl, h->M, h->d.coef);
+  SQ_LAUNCH_CHECK(h);
+  const int nblk = std::min(1024, (h->Nd + 255) / 256);
+  k_contract<<<nblk, 256, 0, s>>>(h->d.mom, h->d.coef, h->d.scal, h->d.v64, h->Nd, g.n_pl, g.dV, h->d.rho, h->d.part);
+  SQ_LAUNCH_CHECK(h);
+  k_contract_final<<<1, 32, 0, s>>>(h->d.part, nblk, h->kT, h->vol, h->d.scal);
+  SQ_LAUNCH_CHECK(h);
+  return SQ_OK;
 }
 
 int run_contraction(sq_handle* h, double mu, double* rho_dev, double* out_host) {

@@ -211,7 +211,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
        const Real* __restrict__ chi, const float* __restrict__ chis, const Real* __restrict__ gdv,
        const int4* __restrict__ brec, const int* __restrict__ slab_n, const int* __restrict__ slab_map, const int* __restrict__ bn,
        const Real* __restrict__ v, const double* __restrict__ scal, int mode, double* __restrict__ Spart,
-       int rows_smem, const double* __restrict__ ncoef) {
+       int rows_smem, const double* __restrict__ ncoef, int* __restrict__ status) {
   // dynamic shared memory: [Ps: rows_smem x 8 FP64][red: nw x 8 x 9 FP64][Pstage: rows_smem x 8]
   // [tn_sm: nw x 16 x 32] (Ps and Pstage only with kSmemP; rows_smem = 0 otherwise)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -224,6 +224,10 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
   // numbering, smap: slab row -> tile row); without it records index the tile rows directly.
   double* Ps = kSmemP ? reinterpret_cast<double*>(smem_raw) : Pn;
   const int nsr = kSmemP ? slab_n[(size_t)tl * g.nslab + slab] : 0;
+  if (kSmemP && nsr > rows_smem) {   // a launch sized for another layout (e.g. a stale graph): refuse
+    if (threadIdx.x == 0) atomicOr(status + kStOverflow, 4);
+    return;
+  }
   const int* smap = slab_map + ((size_t)tl * g.nslab + slab) * g.r_cap;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* red = reinterpret_cast<double*>(smem_raw) + (size_t)rows_smem * kTileB;        // S partials [nw][8][9]
@@ -723,7 +727,7 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
                        int mode) {
   const int rows_smem = int(smem / (kTileB * (sizeof(double) + sizeof(Real))));
   const double* ncoef = (h->bounds_mode == SQ_BOUNDS_PER_NODE) ? h->d.ncoef : nullptr;
-  const int nw = step_warps(h->geo.nbr[0] * h->geo.nbr[2]), nthr = 32 * nw;
+  const int nw = h->step_warps > 0 ? h->step_warps : step_warps(h->geo.nbr[0] * h->geo.nbr[2]), nthr = 32 * nw;
   const size_t smem_warps = size_t(nw) * (kTileB * 9 * sizeof(double) + 16 * 32 * sizeof(Real));
   // The dynamic-size attribute belongs to the function, not the launch, and handles on other
   // host threads launch the same kernel, so every caller sets the same value (the largest
@@ -736,7 +740,7 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmemMax));
       k_step<Real, NO, true, sizeof(Real) == 4><<<grid, nthr, smem, h->stream>>>(
           h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.chi32s, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n,
-          v, h->d.scal, mode, h->wb.Spart, rows_smem, ncoef);
+          v, h->d.scal, mode, h->wb.Spart, rows_smem, ncoef, h->d.status);
       SQ_LAUNCH_CHECK(h);
       return SQ_OK;
     }
@@ -745,14 +749,14 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
                                         kStepSmemMax));
     k_step<Real, NO, true, false><<<grid, nthr, smem, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
                                                                 h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
-                                                                h->d.scal, mode, h->wb.Spart, rows_smem, ncoef);
+                                                                h->d.scal, mode, h->wb.Spart, rows_smem, ncoef, h->d.status);
   } else {
     h->step_variant[2]++;
     SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kStepSmemMax));
     k_step<Real, NO, false, false><<<grid, nthr, smem_warps, h->stream>>>(h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, nullptr, gdv,
                                                               h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, v,
-                                                              h->d.scal, mode, h->wb.Spart, 0, ncoef);
+                                                              h->d.scal, mode, h->wb.Spart, 0, ncoef, h->d.status);
   }
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
@@ -780,15 +784,21 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
   double* Pg[2] = {(double*)h->wb.Pg[0], (double*)h->wb.Pg[1]};
   Real* A = (Real*)h->wb.A;
   Real* W = (Real*)h->wb.W;
-  std::vector<int> nrows;
-  for (const Wave& w : h->waves) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SQ_CUDA_TRY(h, cudaStreamIsCapturing(s, &cap));
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (h->wave_rows.size() != h->waves.size()) {
+    if (capturing) return fail(h, SQ_ERR_STATE, "wave layout not measured before capture");
+    int rc = measure_wave_rows(h);
+    if (rc != SQ_OK) return rc;
+  }
+  for (size_t wi = 0; wi < h->waves.size(); ++wi) {
+    const Wave& w = h->waves[wi];
     int rc = build_wave_lists(h, w);
     if (rc != SQ_OK) return rc;
-    // largest slab projector-row count of the wave sizes the per-slab shared accumulator
-    nrows.resize(size_t(w.ntiles) * g.nslab);
-    SQ_CUDA_TRY(h, cudaMemcpyAsync(nrows.data(), h->wb.slab_n, sizeof(int) * nrows.size(), cudaMemcpyDeviceToHost, s));
-    SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
-    const int rmax = nrows.empty() ? 0 : *std::max_element(nrows.begin(), nrows.end());
+    // largest slab projector-row count of the wave (measured once per layout) sizes the
+    // per-slab shared accumulator
+    const int rmax = h->wave_rows[wi];
     const size_t smem = std::max<size_t>(1, size_t(rmax)) * kTileB * (sizeof(double) + sizeof(Real));
 
     const dim3 gstencil(g.nslab, w.ntiles);
@@ -807,16 +817,17 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
       Real* Tp = T[(j + 2) % 3];
       const int mode = (j == g.n_pl) ? 2 : (j == 0 ? 0 : 1);
       const double vecs = (mode == 0) ? 2.0 : (mode == 1) ? 3.0 : 1.0;   // reads t^j (t^{j-1}), writes t^{j+1}
-      cudaEvent_t ev = timing_begin(h, SQ_K_STENCIL, vecs * col_bytes);
+      cudaEvent_t ev = capturing ? nullptr : timing_begin(h, SQ_K_STENCIL, vecs * col_bytes);
       rc = dispatch_step<Real>(h, w, gstencil, smem, Tc, Tp, Tn, Pg[j % 2], Pg[(j + 1) % 2], W, chi, gdv, v, mode);
       if (rc != SQ_OK) return rc;
       timing_end(h, ev);
-      ev = timing_begin(h, SQ_K_MOMENTS, 0.0);
+      ev = capturing ? nullptr : timing_begin(h, SQ_K_MOMENTS, 0.0);
       k_moments<Real><<<w.ntiles, kThreads, 0, s>>>(g, w, j, Tc, A, Pg[j % 2], h->wb.n_rows, h->wb.Spart, h->d.mom);
       timing_end(h, ev);
       SQ_LAUNCH_CHECK(h);
     }
   }
+  if (capturing) return SQ_OK;   // the status words are read after the graph runs
   {
     int rc = timing_collect(h);
     if (rc != SQ_OK) return rc;
@@ -825,6 +836,69 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
   SQ_CUDA_TRY(h, cudaMemcpyAsync(st, h->d.status, sizeof(st), cudaMemcpyDeviceToHost, s));
   SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
   if (st[kStOverflow]) return fail(h, SQ_ERR_CUDA, "internal list capacity exceeded");
+  if (st[kStBadBounds]) return fail(h, SQ_ERR_CUDA, "spectral bounds are not finite or empty");
+  return SQ_OK;
+}
+
+template <typename Real>
+static int time_step_t(sq_handle* h, int reps, double* ms_out, const Real* chi, const Real* v, const Real* gdv) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  if (h->waves.empty()) {
+    *ms_out = 0.0;
+    return SQ_OK;
+  }
+  if (h->wave_rows.size() != h->waves.size()) {
+    int rc = measure_wave_rows(h);
+    if (rc != SQ_OK) return rc;
+  }
+  const Wave& w = h->waves[0];
+  int rc = build_wave_lists(h, w);
+  if (rc != SQ_OK) return rc;
+  Real* T[3] = {(Real*)h->wb.T[0], (Real*)h->wb.T[1], (Real*)h->wb.T[2]};
+  double* Pg[2] = {(double*)h->wb.Pg[0], (double*)h->wb.Pg[1]};
+  const size_t smem = std::max<size_t>(1, size_t(h->wave_rows[0])) * kTileB * (sizeof(double) + sizeof(Real));
+  const dim3 grid(g.nslab, w.ntiles);
+  // the first launch (mode 0) forms t^1 from t^0, so the timed launches read defined values
+  rc = dispatch_step<Real>(h, w, grid, smem, T[0], T[2], T[1], Pg[0], Pg[1], (Real*)h->wb.W, chi, gdv, v, 0);
+  if (rc != SQ_OK) return rc;
+  cudaEvent_t e0, e1;
+  SQ_CUDA_TRY(h, cudaEventCreate(&e0));
+  SQ_CUDA_TRY(h, cudaEventCreate(&e1));
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && rc == SQ_OK; ++r)
+    rc = dispatch_step<Real>(h, w, grid, smem, T[1], T[0], T[2], Pg[1], Pg[0], (Real*)h->wb.W, chi, gdv, v, 1);
+  cudaEventRecord(e1, s);
+  float ms = 0.f;
+  const cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SQ_OK) return rc;
+  if (e != cudaSuccess) return fail(h, SQ_ERR_CUDA, std::string("step timing: ") + cudaGetErrorString(e));
+  *ms_out = double(ms) / std::max(1, reps);
+  return SQ_OK;
+}
+
+int time_step_launch(sq_handle* h, int reps, double* ms_out) {
+  if (h->precision == SQ_FP64) return time_step_t<double>(h, reps, ms_out, h->d.chi64, h->d.v64, h->d.gdv64);
+  return time_step_t<float>(h, reps, ms_out, h->d.chi32, h->d.v32, h->d.gdv32);
+}
+
+int measure_wave_rows(sq_handle* h) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  std::vector<int> nrows;
+  h->wave_rows.assign(h->waves.size(), 0);
+  for (size_t wi = 0; wi < h->waves.size(); ++wi) {
+    const Wave& w = h->waves[wi];
+    int rc = build_wave_entries(h, w);
+    if (rc != SQ_OK) return rc;
+    nrows.resize(size_t(w.ntiles) * g.nslab);
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(nrows.data(), h->wb.slab_n, sizeof(int) * nrows.size(), cudaMemcpyDeviceToHost, s));
+    SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
+    h->wave_rows[wi] = nrows.empty() ? 0 : *std::max_element(nrows.begin(), nrows.end());
+  }
   return SQ_OK;
 }
 

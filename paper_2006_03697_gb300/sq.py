@@ -31,7 +31,8 @@ EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_node_sums", "sq_fermi_level_sums",
     "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_node_bounds", "sq_moments_copy", "sq_footprint_bytes",
-    "sq_kernel_launches", "sq_step_launch_counts", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate", "sq_server_create", "sq_server_submit", "sq_server_submit_traj", "sq_server_resident",
+    "sq_kernel_launches", "sq_step_launch_counts", "sq_tune_step", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate",
+    "sq_batch_create", "sq_batch_run", "sq_batch_last_error", "sq_batch_destroy", "sq_server_create", "sq_server_submit", "sq_server_submit_traj", "sq_server_resident",
     "sq_update_atoms",
     "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_gauss_density", "sq_green_kubo", "sq_destroy",
     "sq_last_error",
@@ -104,6 +105,8 @@ def lib():
         L.sq_footprint_bytes.restype = C.c_size_t
         L.sq_kernel_launches.argtypes = [H]
         L.sq_kernel_launches.restype = C.c_longlong
+        L.sq_tune_step.argtypes = [H, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
+        L.sq_tune_step.restype = C.c_int
         L.sq_step_launch_counts.argtypes = [H, C.POINTER(C.c_longlong)]
         L.sq_step_launch_counts.restype = C.c_int
         L.sq_kernel_timing.argtypes = [H, C.c_int]
@@ -116,6 +119,14 @@ def lib():
         L.sq_fermi_level_noalloc.restype = C.c_int
         L.sq_batch_evaluate.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         L.sq_batch_evaluate.restype = C.c_int
+        L.sq_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
+        L.sq_batch_create.restype = C.c_int
+        L.sq_batch_run.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.sq_batch_run.restype = C.c_int
+        L.sq_batch_last_error.argtypes = [C.c_void_p]
+        L.sq_batch_last_error.restype = C.c_char_p
+        L.sq_batch_destroy.argtypes = [C.c_void_p]
+        L.sq_batch_destroy.restype = None
         L.sq_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]
         L.sq_server_create.restype = C.c_int
         L.sq_server_submit.argtypes = [C.c_void_p, C.POINTER(sq_instance_desc), C.c_longlong]
@@ -362,6 +373,56 @@ def sq_step_launch_counts(h):
     return tuple(int(x) for x in c)
 
 
+def sq_tune_step(h, n_warps: int = 0, wave_tiles: int = 0, reps: int = 0):
+    """Sets the step kernel's warps per block and tiles per wave; with reps > 0 returns the
+    timed milliseconds per tile and step, else None."""
+    ms = C.c_double(0.0)
+    _check(lib().sq_tune_step(h, int(n_warps), int(wave_tiles), int(reps), C.byref(ms) if reps > 0 else None), h)
+    return ms.value if reps > 0 else None
+
+
+TUNE_CACHE = Path(__file__).resolve().parent / "_lib" / "step_tune.json"
+
+
+def autotune_step(h, inst: dict, precision, candidates_warps=(4, 5, 6, 7, 8), wave_fractions=(1, 2, 4),
+                  reps: int = 3, cache: Path | None = TUNE_CACHE):
+    """Chooses warps per step block and tiles per wave for this handle's geometry by timing the
+    candidates (sq_tune_step) and keeps the fastest; the choice is cached per geometry key
+    (precision, n_o, region half-widths m, tiles) in a JSON file beside the built library, so the
+    next handle of the same shape takes it without timing. Returns (key, choice, timings)."""
+    import json
+    n = np.asarray(inst["n"], dtype=np.int64)
+    h_ = np.asarray(inst["L"], dtype=np.float64) / n
+    m = np.floor(float(inst["r_cut"]) / h_ + 1e-9).astype(int)
+    tiles = int(np.prod((n + 1) // 2))
+    key = f"p{int(precision)}_no{int(inst['n_o'])}_m{'x'.join(str(x) for x in m)}_t{tiles}"
+    table = {}
+    if cache is not None and cache.exists():
+        try:
+            table = json.loads(cache.read_text())
+        except ValueError:
+            table = {}
+    if key in table:
+        w, wt = table[key]["warps"], table[key]["wave_tiles"]
+        sq_tune_step(h, w, wt, 0)
+        return key, table[key], None
+    times = {}
+    base = sq_tune_step(h, 0, 0, reps)                       # the default settings first
+    times[(0, 0)] = base
+    for frac in wave_fractions:
+        wt = 0 if frac == 1 else max(1, tiles // frac)
+        for w in candidates_warps:
+            times[(w, wt)] = sq_tune_step(h, w, wt, reps)
+    (w, wt), best = min(times.items(), key=lambda kv: kv[1])
+    sq_tune_step(h, w, wt, 0)
+    choice = {"warps": w, "wave_tiles": wt, "ms_per_tile": best, "default_ms_per_tile": base}
+    if cache is not None:
+        table[key] = choice
+        cache.parent.mkdir(exist_ok=True)
+        cache.write_text(json.dumps(table, indent=1))
+    return key, choice, {f"{k[0]}w_{k[1]}t": v for k, v in times.items()}
+
+
 def sq_kernel_timing(h, enable: bool):
     _check(lib().sq_kernel_timing(h, 1 if enable else 0), h)
 
@@ -449,6 +510,33 @@ def sq_green_kubo(sigma, dt: float, volume: float, kT: float, max_lag: int, stre
     if rc != SQ_OK:
         raise SQError(rc, sq_last_error(None))
     return eta, acf
+
+
+class Batch:
+    """sq_batch_* : one CUDA graph evaluating a batch of handles (argument marshalling only)."""
+
+    def __init__(self, handles):
+        self.n = len(handles)
+        arr = (C.c_void_p * self.n)(*[h.value for h in handles])
+        self.b = C.c_void_p()
+        rc = lib().sq_batch_create(arr, self.n, C.byref(self.b))
+        if rc != SQ_OK:
+            raise SQError(rc, "sq_batch_create failed: " + " / ".join(sq_last_error(h) for h in handles))
+
+    def run(self):
+        mu = np.zeros(self.n)
+        en = (sq_energies * self.n)()
+        sig = np.zeros((self.n, 9))
+        rc = lib().sq_batch_run(self.b, mu.ctypes.data, en, sig.ctypes.data)
+        if rc != SQ_OK:
+            raise SQError(rc, lib().sq_batch_last_error(self.b).decode(errors="replace"))
+        out = [{k: getattr(en[i], k) for k, _ in sq_energies._fields_} for i in range(self.n)]
+        return mu, out, sig.reshape(self.n, 3, 3)
+
+    def close(self):
+        if self.b:
+            lib().sq_batch_destroy(self.b)
+            self.b = C.c_void_p()
 
 
 class Server:
