@@ -42,6 +42,18 @@ def test_noalloc_fermi_level_matches_regular_entry_point():
         results.append(mu)
     assert results[0] != results[1]
 
+    # a moment table that cannot bracket N_e (all zero: N(mu) = 0 everywhere) gives NaN, and
+    # the next regular call is unaffected by the scratch this one left
+    zeros = torch.zeros((nd, n_pl + 1, sq.SQ_N_MOMENTS), dtype=torch.float64, device="cuda")
+    sq.sq_fermi_level_noalloc(zeros.data_ptr(), nd, n_pl, lo, hi, inst["kT"], inst["n_e"], 2048, stream,
+                              mu_dev.data_ptr())
+    torch.cuda.synchronize()
+    assert np.isnan(float(mu_dev.item()))
+    sq.sq_fermi_level_noalloc(mom_dev.data_ptr(), nd, n_pl, lo, hi, inst["kT"], inst["n_e"], 2048, stream,
+                              mu_dev.data_ptr())
+    torch.cuda.synchronize()
+    assert abs(float(mu_dev.item()) - results[1]) <= 1e-12 * max(1.0, abs(results[1]))
+
     # sizes beyond the fixed scratch are rejected before any launch
     with pytest.raises(sq.SQError) as ei:
         sq.sq_fermi_level_noalloc(mom_dev.data_ptr(), nd, 5000, lo, hi, 1.0, 1.0, 2048, None, mu_dev.data_ptr())
