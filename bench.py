@@ -53,9 +53,9 @@ def parse():
                     help="seeded node columns per step of --impl reference")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="timed evaluations of the plain FP64 GPU path (after one warm-up)")
-    ap.add_argument("--serve-requests", type=int, default=24,
+    ap.add_argument("--serve-requests", type=int, default=30,
                     help="requests in the served-stream measurement (0 disables it)")
-    ap.add_argument("--serve-trajectories", type=int, default=8)
+    ap.add_argument("--serve-trajectories", type=int, default=10)
     ap.add_argument("--batch", type=int, default=8,
                     help="instances in the batched-snapshot measurement (0 disables it)")
     ap.add_argument("--no-large", dest="large", action="store_false",
@@ -238,19 +238,20 @@ def cpu_oracle_rate(inst, n_nodes: int):
         timer.close()
 
 
-def serve_stream(sq, n_req: int, prec: int, n_traj: int = 8, max_inflight: int = 4, load: float = 0.7):
+def serve_stream(sq, n_req: int, prec: int, n_traj: int = 10, max_inflight: int = 4, load: float = 0.7):
     """A served stream of quantum-MD snapshots with the size mix of the served workload: n_traj
-    trajectories whose cells are drawn as the batched snapshots (32 ... 512 H at 0.0375 / bohr^3,
-    kT in [1.6, 6.3], n_pl in [30, 80], R_cut in [3, 5]) with 20 % of them 512-atom, 80^3-node
-    cells; request i is the next snapshot of trajectory i mod n_traj (atoms moved by
-    N(0, 0.05^2) bohr, V_eff with them) and keeps that trajectory's handle resident on the
-    device (sq_server_submit_traj). Arrivals are Poisson at `load` x the saturated rate measured
-    on the first round of requests. Reports p50 / p99 latency (submit to result) and evals/s."""
+    trajectories whose cells are drawn as the batched snapshots (32 ... 256 H at 0.0375 / bohr^3,
+    kT in [1.6, 6.3], n_pl in [30, 80], R_cut in [3, 5]), 20 % of them (rounded) 512-atom,
+    80^3-node cells; request i is the next snapshot of trajectory i mod n_traj (atoms moved by
+    N(0, 0.05^2) bohr, V_eff with them), so 20 % of the requests are 512-atom cells, and keeps
+    that trajectory's handle resident on the device (sq_server_submit_traj). Arrivals are Poisson
+    at `load` x the saturated rate measured on the first round of requests. Reports p50 / p99
+    latency (submit to result) and evals/s."""
     import numpy as np
     from workloads import gaussian_veff, make_batch, perturb_positions
-    base = make_batch(config=5, count=n_traj, p_large=0.2)
-    if not any(len(b["pos"]) == 512 for b in base):   # keep one large cell in the mix
-        base[-1] = make_batch(config=5, count=1, start=100, atom_choices=(512,))[0]
+    n_large = max(1, int(round(0.2 * n_traj)))
+    base = make_batch(config=5, count=n_traj - n_large, atom_choices=(32, 64, 128, 256))
+    base += make_batch(config=5, count=n_large, start=100, atom_choices=(512,))
     rng = np.random.Generator(np.random.PCG64(5000))
     state = [dict(b) for b in base]
     reqs = []
@@ -294,7 +295,8 @@ def serve_stream(sq, n_req: int, prec: int, n_traj: int = 8, max_inflight: int =
             "p99_ms": float(np.percentile(lat, 99)), "arrival_rate_per_s": rate, "saturated_evals_per_s": sat,
             "max_inflight": max_inflight, "trajectories": n_traj, "atoms_per_trajectory": sizes,
             "resident_handles_at_end": resident,
-            "workload": "served mix: trajectories of the batched snapshots (32-512 H, 20 % 512-atom 80^3 cells), "
+            "workload": f"served mix: {n_traj} trajectories of the batched snapshots (32-256 H, and {n_large} of "
+                        "512-atom 80^3 cells: 20 % of the requests), "
                         "consecutive snapshots moved by N(0, 0.05^2) bohr with resident device state, Poisson "
                         f"arrivals at {load} x the saturated rate; the first round (one request per trajectory, "
                         "setup included) sets the rate and is not in the latency statistics"}

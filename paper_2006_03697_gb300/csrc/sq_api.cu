@@ -424,6 +424,7 @@ size_t sq_footprint_bytes(const sq_instance_desc* desc) {
 }
 
 int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
+  sq::NvtxRange nvtx("sq_setup");
   if (!out) { g_setup_err = "out is NULL"; return SQ_ERR_INVALID_ARG; }
   *out = nullptr;
   std::string why;
@@ -622,12 +623,15 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
 
 int sq_moments(sq_handle* h) {
   if (!h) return SQ_ERR_INVALID_ARG;
+  sq::NvtxRange nvtx("sq_moments");
   int rc;
   if (h->bounds_mode == SQ_BOUNDS_LANCZOS) {   // bounds are part of every sweep
+    sq::NvtxRange nb("bounds: Lanczos");
     rc = sq::run_lanczos(h);
     if (rc != SQ_OK) return rc;
     h->bounds_ready = true;
   } else if (h->bounds_mode == SQ_BOUNDS_PER_NODE) {
+    sq::NvtxRange nb("bounds: per-node Lanczos");
     rc = sq::run_lanczos_nodes(h);
     if (rc != SQ_OK) return rc;
     h->bounds_ready = true;
@@ -641,12 +645,14 @@ int sq_moments(sq_handle* h) {
 int sq_fermi_level(sq_handle* h, double* mu_out) {
   if (!h) return SQ_ERR_INVALID_ARG;
   if (!h->moments_ready) return sq::fail(h, SQ_ERR_STATE, "sq_fermi_level before sq_moments");
+  sq::NvtxRange nvtx("sq_fermi_level");
   if (h->bounds_mode == SQ_BOUNDS_PER_NODE) return sq::run_fermi_nodes(h, mu_out);
   return sq::run_fermi(h, mu_out);
 }
 
 int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff) {
   if (!h) return SQ_ERR_INVALID_ARG;
+  sq::NvtxRange nvtx("sq_update_atoms");
   const sq::Geo& g = h->geo;
   if (!v_eff || (g.n_atoms > 0 && !pos)) return sq::fail(h, SQ_ERR_INVALID_ARG, "pos or v_eff is NULL");
   for (int i = 0; i < h->Nd; ++i)
@@ -704,6 +710,7 @@ static int contraction_common(sq_handle* h, double mu, double* rho_dev, sq_energ
   if (!h) return SQ_ERR_INVALID_ARG;
   if (!h->moments_ready) return sq::fail(h, SQ_ERR_STATE, "contraction before sq_moments");
   if (!std::isfinite(mu)) return sq::fail(h, SQ_ERR_INVALID_ARG, "mu is not finite");
+  sq::NvtxRange nvtx("contraction");
   double out[16];
   double* sums = (e_out || sigma_host || pressure_host) ? out : nullptr;
   int rc = (h->bounds_mode == SQ_BOUNDS_PER_NODE) ? sq::run_contraction_nodes(h, mu, rho_dev, sums)

@@ -171,6 +171,7 @@ int sq_batch_create(sq_handle* const* hs, int n, sq_batch** out) {
 
 int sq_batch_run(sq_batch* b, double* mu_out, sq_energies* e_out, double* sigma_out) {
   if (!b) return SQ_ERR_INVALID_ARG;
+  sq::NvtxRange nvtx("sq_batch_run");
   const int n = int(b->hs.size());
   bool stale = !b->exec;
   for (int i = 0; i < n; ++i)

@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -201,6 +202,16 @@ struct sq_handle {
 };
 
 namespace sq {
+
+// Named host-side range around a phase of the pipeline (setup, bounds, each sweep wave, Fermi
+// search, contraction, batch, request), shown on a profiler's timeline; header-only NVTX v3,
+// which costs nothing when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Spectral scaling of the recurrence from bounds [lo, hi] (sq_api.cu): writes the step
 // coefficients and the effective bounds used by the Fermi search and the contraction.

@@ -99,6 +99,7 @@ void finish(sq_server* s, sq_result& res, Request* rq) {
 }
 
 void evaluate(sq_handle* h, sq_result& res, int rc) {
+  sq::NvtxRange nvtx("served request");
   if (rc == SQ_OK) rc = sq_moments(h);
   if (rc == SQ_OK) rc = sq_fermi_level(h, &res.mu);
   if (rc == SQ_OK) rc = sq_density_energy_stress(h, res.mu, nullptr, &res.energies, res.sigma);

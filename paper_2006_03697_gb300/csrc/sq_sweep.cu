@@ -793,6 +793,7 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
     if (rc != SQ_OK) return rc;
   }
   for (size_t wi = 0; wi < h->waves.size(); ++wi) {
+    NvtxRange nvtx("sweep wave");
     const Wave& w = h->waves[wi];
     int rc = build_wave_lists(h, w);
     if (rc != SQ_OK) return rc;
