@@ -354,7 +354,10 @@ void sq_server_destroy(sq_server* s);
  * E_band = 2 sum_q sum_i w_qi theta_qi g(theta_qi). Independent of sq_moments (it neither needs
  * nor changes the Chebyshev moments; it rebuilds the per-wave lists). k in 1..128 (capped at
  * the region dimension). Host outputs: mu_out, rho_out [N_d] (x fastest), e_band_out, each may
- * be NULL. Allocates and frees its own device scratch; synchronises the stream.
+ * be NULL. Allocates and frees its own device scratch, not counted by sq_footprint_bytes: Krylov
+ * waves of at most 16 GiB (and at most 80 % of the free device memory; fewer tiles per wave when
+ * less is free) plus 2 N_d k + N_d doubles for the Gauss nodes, weights and density; synchronises
+ * the stream.
  * Errors: SQ_ERR_INVALID_ARG (k), SQ_ERR_OOM, SQ_ERR_NO_BRACKET, SQ_ERR_CUDA. */
 int sq_gauss_density(sq_handle* h, int k, double* mu_out, double* rho_out, double* e_band_out);
 

@@ -108,6 +108,44 @@ __global__ void k_gauss_count(int ncols, int k, const double* __restrict__ theta
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// Smallest and largest Gauss node with a non-zero weight: per block, then (k_gauss_minmax_final)
+// over the blocks; the Fermi bracket's ends, without copying the N_d k nodes to the host.
+__global__ void k_gauss_minmax(int n, const double* __restrict__ theta, const double* __restrict__ wgt,
+                               double* __restrict__ part) {
+  __shared__ double slo[256], shi[256];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (wgt[i] != 0.0) {
+      lo = fmin(lo, theta[i]);
+      hi = fmax(hi, theta[i]);
+    }
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + st]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + st]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = slo[0];
+    part[2 * blockIdx.x + 1] = shi[0];
+  }
+}
+
+__global__ void k_gauss_minmax_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int b = 0; b < nblk; ++b) {
+    lo = fmin(lo, part[2 * b]);
+    hi = fmax(hi, part[2 * b + 1]);
+  }
+  out[0] = lo;
+  out[1] = hi;
+}
+
 // out[0] = sum of part[0..n) in order (one thread)
 __global__ void k_gauss_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -159,7 +197,15 @@ static int gauss_t(sq_handle* h, int k, double* mu_out, double* rho_host, double
   // list capacity of a sweep wave
   const size_t per_tile = ((size_t)(k + 2) * g.Upts + (size_t)g.r_cap) * g.B * sizeof(Real) +
                           (size_t)g.B * (5 * k + 8) * sizeof(double);
-  const int wt = int(std::max<size_t>(1, std::min<size_t>((size_t(16) << 30) / per_tile, (size_t)h->wave_cap)));
+  // at most 16 GiB, and at most 80 % of the free device memory, of Krylov waves
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = size_t(16) << 30;
+  }
+  const size_t fixed = 2 * sizeof(double) * (size_t)g.n_tiles * g.B * k + sizeof(double) * (size_t)h->Nd;
+  const size_t wave_budget = std::min<size_t>(size_t(16) << 30, free_b > fixed ? (free_b - fixed) / 10 * 8 : 0);
+  const int wt = int(std::max<size_t>(1, std::min<size_t>(wave_budget / per_tile, (size_t)h->wave_cap)));
   const int ncols_all = g.n_tiles * g.B;
   std::vector<void*> bufs;
   auto alloc = [&](void** p, size_t bytes) -> bool {
@@ -183,7 +229,7 @@ static int gauss_t(sq_handle* h, int k, double* mu_out, double* rho_host, double
       !alloc((void**)&C, sizeof(double) * (size_t)wt * g.B * (5 * k + 8)) ||
       !alloc((void**)&theta, sizeof(double) * (size_t)ncols_all * k) ||
       !alloc((void**)&wgt, sizeof(double) * (size_t)ncols_all * k) ||
-      !alloc((void**)&part, sizeof(double) * nblk) || !alloc((void**)&sum, sizeof(double)) ||
+      !alloc((void**)&part, sizeof(double) * nblk) || !alloc((void**)&sum, 2 * sizeof(double)) ||
       !alloc((void**)&rho, sizeof(double) * h->Nd)) {
     release();
     return fail(h, SQ_ERR_OOM, "device allocation for the Gauss quadrature failed");
@@ -203,16 +249,23 @@ static int gauss_t(sq_handle* h, int k, double* mu_out, double* rho_host, double
                                                 wgt + (size_t)t0 * g.B * k, h->d.status);
     if (cudaGetLastError() != cudaSuccess) rc = fail(h, SQ_ERR_CUDA, "k_gauss_eig launch failed");
   }
-  // Fermi level: bisection with the Clenshaw-Curtis path's rule
+  // Fermi level: bisection with the Clenshaw-Curtis path's rule; the bracket from the extreme
+  // weighted Gauss nodes (device reduction, two doubles to the host)
   double tmin = 0.0, tmax = 0.0;
   if (rc == SQ_OK) {
-    std::vector<double> th((size_t)ncols_all * k);
-    if (cudaMemcpyAsync(th.data(), theta, sizeof(double) * th.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    const int mblk = std::min(nblk / 2, std::max(1, (ncols_all * k + 255) / 256));
+    double ext[2];
+    k_gauss_minmax<<<mblk, 256, 0, s>>>(ncols_all * k, theta, wgt, part);
+    k_gauss_minmax_final<<<1, 32, 0, s>>>(part, mblk, sum);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(ext, sum, sizeof(ext), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
-      rc = fail(h, SQ_ERR_CUDA, "copy of the Gauss nodes failed");
+      rc = fail(h, SQ_ERR_CUDA, "Gauss node extremes failed");
+    } else if (!(ext[0] <= ext[1])) {
+      rc = fail(h, SQ_ERR_NO_BRACKET, "no Gauss node carries weight");
     } else {
-      tmin = *std::min_element(th.begin(), th.end());
-      tmax = *std::max_element(th.begin(), th.end());
+      tmin = ext[0];
+      tmax = ext[1];
     }
   }
   auto count = [&](double mu, double* out) -> int {
