@@ -298,6 +298,11 @@ int sq_batch_evaluate(sq_handle* const* hs, int n, int max_concurrent, double* m
  * sq_last_error, sq_batch_last_error says which). */
 typedef struct sq_batch sq_batch;
 int sq_batch_create(sq_handle* const* hs, int n, sq_batch** out);
+/* The graph's schedule: members i, i + C, i + 2C, ... run one after another as chain i, the C
+ * chains side by side (C = chains; 0 or >= n: every member in its own branch, the default; 1:
+ * all members in turn). Captures the graph again. Results do not depend on it. Errors:
+ * SQ_ERR_INVALID_ARG, SQ_ERR_CUDA. */
+int sq_batch_set_chains(sq_batch* b, int chains);
 int sq_batch_run(sq_batch* b, double* mu_out, sq_energies* e_out, double* sigma_out);
 const char* sq_batch_last_error(const sq_batch* b);
 void sq_batch_destroy(sq_batch* b);

@@ -58,6 +58,7 @@ extern "C" int sq_batch_evaluate(sq_handle* const* hs, int n, int max_concurrent
 
 struct sq_batch {
   std::vector<sq_handle*> hs;
+  int chains = 0;                       // parallel branches of the graph (members round-robin)
   std::vector<std::vector<int>> rows;   // wave layouts the graph was captured with
   cudaStream_t s0 = nullptr;
   cudaGraph_t graph = nullptr;
@@ -103,18 +104,23 @@ int capture(sq_batch* b) {
   }
   int rc = SQ_OK;
   if (cudaEventRecord(b->evs[0], b->s0) != cudaSuccess) rc = SQ_ERR_CUDA;
+  // members i, i + C, i + 2C, ... form chain i (each waits for the previous one of its chain);
+  // the chains run side by side and all join the origin stream at the end
+  const int C = std::max(1, std::min(n, b->chains > 0 ? b->chains : n));
+  std::vector<cudaEvent_t> last(C, b->evs[0]);
   for (int i = 0; i < n && rc == SQ_OK; ++i) {
     sq_handle* h = b->hs[i];
-    if (cudaStreamWaitEvent(h->stream, b->evs[0], 0) != cudaSuccess) { rc = SQ_ERR_CUDA; break; }
+    if (cudaStreamWaitEvent(h->stream, last[i % C], 0) != cudaSuccess) { rc = SQ_ERR_CUDA; break; }
     rc = pipeline_device(h);
     if (rc != SQ_OK) {
       b->err = std::string("instance ") + std::to_string(i) + ": " + sq_last_error(h);
       break;
     }
-    if (cudaEventRecord(b->evs[i + 1], h->stream) != cudaSuccess ||
-        cudaStreamWaitEvent(b->s0, b->evs[i + 1], 0) != cudaSuccess)
-      rc = SQ_ERR_CUDA;
+    if (cudaEventRecord(b->evs[i + 1], h->stream) != cudaSuccess) rc = SQ_ERR_CUDA;
+    last[i % C] = b->evs[i + 1];
   }
+  for (int c = 0; c < C && rc == SQ_OK; ++c)
+    if (cudaStreamWaitEvent(b->s0, last[c], 0) != cudaSuccess) rc = SQ_ERR_CUDA;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->s0, &g);   // always leave capture mode
   if (rc == SQ_OK && e != cudaSuccess) rc = SQ_ERR_CUDA;
@@ -219,6 +225,17 @@ int sq_batch_run(sq_batch* b, double* mu_out, sq_energies* e_out, double* sigma_
     if (sigma_out) std::memcpy(sigma_out + 9 * (size_t)i, o + 4, 9 * sizeof(double));
   }
   return first;
+}
+
+int sq_batch_set_chains(sq_batch* b, int chains) {
+  if (!b || chains < 0) return SQ_ERR_INVALID_ARG;
+  b->chains = chains;
+  for (sq_handle* h : b->hs)
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return SQ_ERR_CUDA;
+    }
+  return capture(b);
 }
 
 const char* sq_batch_last_error(const sq_batch* b) {

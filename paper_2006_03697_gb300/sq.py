@@ -32,7 +32,7 @@ EXPORTED = [
     "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_node_bounds", "sq_moments_copy", "sq_footprint_bytes",
     "sq_kernel_launches", "sq_step_launch_counts", "sq_tune_step", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate",
-    "sq_batch_create", "sq_batch_run", "sq_batch_last_error", "sq_batch_destroy", "sq_server_create", "sq_server_submit", "sq_server_submit_traj", "sq_server_resident",
+    "sq_batch_create", "sq_batch_set_chains", "sq_batch_run", "sq_batch_last_error", "sq_batch_destroy", "sq_server_create", "sq_server_submit", "sq_server_submit_traj", "sq_server_resident",
     "sq_update_atoms",
     "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_gauss_density", "sq_green_kubo", "sq_destroy",
     "sq_last_error",
@@ -121,6 +121,8 @@ def lib():
         L.sq_batch_evaluate.restype = C.c_int
         L.sq_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
         L.sq_batch_create.restype = C.c_int
+        L.sq_batch_set_chains.argtypes = [C.c_void_p, C.c_int]
+        L.sq_batch_set_chains.restype = C.c_int
         L.sq_batch_run.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.sq_batch_run.restype = C.c_int
         L.sq_batch_last_error.argtypes = [C.c_void_p]
@@ -522,6 +524,12 @@ class Batch:
         rc = lib().sq_batch_create(arr, self.n, C.byref(self.b))
         if rc != SQ_OK:
             raise SQError(rc, "sq_batch_create failed: " + " / ".join(sq_last_error(h) for h in handles))
+
+    def set_chains(self, chains: int):
+        """Graph schedule: `chains` parallel chains of members (0 = all concurrent, 1 = serial)."""
+        rc = lib().sq_batch_set_chains(self.b, int(chains))
+        if rc != SQ_OK:
+            raise SQError(rc, lib().sq_batch_last_error(self.b).decode(errors="replace"))
 
     def run(self):
         mu = np.zeros(self.n)

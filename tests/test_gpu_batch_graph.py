@@ -54,6 +54,13 @@ def test_graph_batch_equals_alone_and_relaunches(sq):
         # after the launch the members hold their moments: another contraction works on them
         rho, e2, s2 = sq.sq_density_energy_stress(hs[0], mu[0], int(np.prod(members[0][0]["n"])))
         assert abs(e2["F"] - refs[0]["F"]) <= 1e-10 * abs(refs[0]["F"])
+        # any schedule of the graph (serial chain, two chains) gives the same results
+        for chains in (1, 2):
+            batch.set_chains(chains)
+            mu_c, en_c, sig_c = batch.run()
+            for i, ((inst, prec, b), ref) in enumerate(zip(members, refs)):
+                _check(mu_c[i], en_c[i], sig_c[i], ref, 1e-10 if prec == sq.SQ_FP64 else 1e-7)
+        batch.set_chains(0)
         # the next snapshot of member 1 through the same graph
         rng = np.random.Generator(np.random.PCG64(77))
         nxt = dict(members[1][0])
