@@ -57,6 +57,10 @@ TINY = {
     "no6_truncated": dict(seed=4, n=(4, 4, 4), h=(0.5, 0.5, 0.5), n_atoms=2, n_o=6, r_cut=2.5, n_pl=12),
     # single node per cell along x, window wraps the cell many times
     "thin_cell": dict(seed=5, n=(1, 3, 2), h=(0.9, 0.8, 0.7), n_atoms=1, n_o=2, r_cut=2.0, n_pl=8),
+    # 8th- and 10th-order stencils (the remaining compiled stencil orders), windows wrapping a
+    # small cell
+    "no4": dict(seed=8, n=(5, 4, 6), h=(0.6, 0.6, 0.6), n_atoms=2, n_o=4, r_cut=2.0, n_pl=12),
+    "no5": dict(seed=9, n=(4, 5, 4), h=(0.55, 0.55, 0.55), n_atoms=2, n_o=5, r_cut=2.3, n_pl=10),
     # 5 channels per atom (two s, one p): channel groups beyond 4 (the scalar projector phases
     # in both precisions)
     "five_channels": dict(seed=6, n=(5, 5, 4), h=(0.7, 0.7, 0.7), n_atoms=2, n_o=3, r_cut=2.1, n_pl=14,

@@ -5,6 +5,7 @@ Each rank takes the node set the library's tile-range rule gives it (sq.partitio
 the FP64 oracle's moments of those nodes only, and runs the exchange steps of the partitioned
 path: one allreduce of the node sums R^j before the Fermi search, one of the partial energies,
 pressure and sigma after the contraction. The result must equal the whole-cell oracle."""
+import datetime
 import os
 import socket
 
@@ -88,3 +89,38 @@ def test_partitioned_sums_equal_the_whole_cell_gloo():
         assert np.allclose(tot[len(sq.PART_SUM_KEYS):].reshape(3, 3), ref["sigma"], rtol=1e-11, atol=1e-14)
     rho = np.asarray(out[0]["rho"]) + np.asarray(out[1]["rho"])
     assert np.allclose(rho, ref["rho"], rtol=1e-12, atol=1e-14)
+
+
+def _worker_dies(rank, world, port, out):
+    """Rank 1 fails before the exchange of the node sums (a sweep that raised); rank 0's
+    allreduce must end with an error within the process group's timeout, not hang."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)                                   # leaves between steps, nothing in flight
+    inst = tiny_instance(**CASE)
+    prob = orc.Problem(inst)
+    nodes = sq.partition_nodes(inst["n"], rank, world)
+    mom = np.zeros((prob.Nd, prob.n_pl + 1, orc.N_MOM))
+    mom[nodes] = orc.all_moments(prob, *BOUNDS, nodes=nodes)
+    try:
+        _allreduce(mom[:, :, 0].sum(axis=0))
+        out[rank] = "no error"
+    except Exception as e:                            # the failed peer is reported, not waited for
+        out[rank] = "error: " + type(e).__name__
+    os._exit(0)
+
+
+def test_failed_rank_is_reported_to_its_peer_gloo():
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_dies, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert procs[1].exitcode == 3
+    assert procs[0].exitcode == 0
+    assert out[0].startswith("error"), out[0]
