@@ -472,6 +472,7 @@ def run_ours(args):
 
     def finish(hh, mu, en):
         """Whole-cell results of a partitioned handle: the parts' sums (one allreduce)."""
+        stream.synchronize()   # sigma_dev is written on the library stream
         keys = ("E_band", "E_s", "E_nl", "N_check")
         tot = allreduce(np.concatenate([[en[k] for k in keys], sig_dev.cpu().numpy()]))
         out = {k: float(tot[i]) for i, k in enumerate(keys)}
@@ -492,7 +493,7 @@ def run_ours(args):
     en = step()
     # autotuner: warps per step block and tiles per wave for this geometry (cached per shape),
     # chosen before the warm-up and the timed region
-    tune_key, tune_choice, _ = sq.autotune_step(h, inst, prec)
+    tune_key, tune_choice, _ = sq.autotune_step(h, inst, prec, partition=part)
     for _ in range(max(0, args.warmup - 1)):
         en = step()
     torch.cuda.synchronize()
@@ -575,7 +576,8 @@ def run_ours(args):
         "clocks": clk, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
         "kernels": kern, "energies": {k: en[k] for k in ("E_band", "E_s", "E_nl", "F", "N_check", "mu")},
         "sigma": sig_dev.cpu().numpy().reshape(3, 3).tolist(),
-        "pressure_app_a": sq.sq_pressure(h, en["mu"])[0],
+        "pressure_app_a": (sq.sq_pressure(h, en["mu"])[0] if dist is None
+                           else float(allreduce(np.array([sq.sq_pressure(h, en["mu"])[0]]))[0])),
     }
     if args.fp64_compare and rank == 0 and world == 1:
         # the plain FP64 GPU path (same library, SQ_FP64) on the same input: one untimed warm-up

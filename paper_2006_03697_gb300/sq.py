@@ -387,7 +387,7 @@ TUNE_CACHE = Path(__file__).resolve().parent / "_lib" / "step_tune.json"
 
 
 def autotune_step(h, inst: dict, precision, candidates_warps=(4, 5, 6, 7, 8), wave_fractions=(1, 2, 4),
-                  reps: int = 3, cache: Path | None = TUNE_CACHE):
+                  reps: int = 3, cache: Path | None = TUNE_CACHE, partition=None):
     """Chooses warps per step block and tiles per wave for this handle's geometry by timing the
     candidates (sq_tune_step) and keeps the fastest; the choice is cached per geometry key
     (precision, n_o, region half-widths m, tiles) in a JSON file beside the built library, so the
@@ -397,6 +397,9 @@ def autotune_step(h, inst: dict, precision, candidates_warps=(4, 5, 6, 7, 8), wa
     h_ = np.asarray(inst["L"], dtype=np.float64) / n
     m = np.floor(float(inst["r_cut"]) / h_ + 1e-9).astype(int)
     tiles = int(np.prod((n + 1) // 2))
+    if partition is not None:                                # this part's tile range only
+        r, c = int(partition[0]), int(partition[1])
+        tiles = tiles * (r + 1) // c - tiles * r // c
     key = f"p{int(precision)}_no{int(inst['n_o'])}_m{'x'.join(str(x) for x in m)}_t{tiles}"
     table = {}
     if cache is not None and cache.exists():
@@ -419,9 +422,14 @@ def autotune_step(h, inst: dict, precision, candidates_warps=(4, 5, 6, 7, 8), wa
     sq_tune_step(h, w, wt, 0)
     choice = {"warps": w, "wave_tiles": wt, "ms_per_tile": best, "default_ms_per_tile": base}
     if cache is not None:
+        import os
+        import tempfile
         table[key] = choice
         cache.parent.mkdir(exist_ok=True)
-        cache.write_text(json.dumps(table, indent=1))
+        fd, tmp = tempfile.mkstemp(dir=str(cache.parent), suffix=".json")   # atomic: ranks may share the file
+        with os.fdopen(fd, "w") as f:
+            f.write(json.dumps(table, indent=1))
+        os.replace(tmp, cache)
     return key, choice, {f"{k[0]}w_{k[1]}t": v for k, v in times.items()}
 
 
