@@ -32,8 +32,10 @@
  *   - sigma is returned row-major 3x3 in Ha/bohr^3 (sigma[3*a + b]).
  *   - Every call returns an int status (SQ_OK = 0). The library never aborts or traps; on
  *     error sq_last_error() describes the failure. No kernel of the library waits on another
- *     kernel or on the host, so no call can hang on the device; SQ_ERR_TIMEOUT is reserved
- *     and no call returns it at present.
+ *     kernel or on the host. The one device wait is the TMA-staged step's wait for its own
+ *     copies into shared memory (SQ_MIXED with SQ_STEP_KERNEL=staged): it gives up after about
+ *     2e9 clock cycles (about a second), and the sweep then returns SQ_ERR_TIMEOUT (sq_moments,
+ *     sq_batch_run).
  *   - The caller owns every host buffer passed in or out; the library copies inputs during
  *     sq_setup and owns all device memory of a handle until sq_destroy.
  *   - A handle is used by one host thread at a time. Work is issued on desc->stream
@@ -54,7 +56,7 @@ extern "C" {
 #define SQ_ERR_OOM 2           /* device or host allocation failed                    */
 #define SQ_ERR_CUDA 3          /* a CUDA runtime call failed                           */
 #define SQ_ERR_NO_BRACKET 4    /* N(mu) - N_e has no sign change on the bisection bracket */
-#define SQ_ERR_TIMEOUT 5       /* reserved for a bounded device wait (none at present)  */
+#define SQ_ERR_TIMEOUT 5       /* a bounded device wait (staged step copies) ran out    */
 #define SQ_ERR_STATE 6         /* call out of order (e.g. contraction before moments)  */
 
 /* precision modes */
@@ -215,14 +217,20 @@ size_t sq_footprint_bytes(const sq_instance_desc* desc);
 /* Number of CUDA kernels the handle launched since sq_setup (all calls). */
 long long sq_kernel_launches(const sq_handle* h);
 
-/* Launches of the Chebyshev step kernel since sq_setup, by variant, into counts[3] (host):
+/* Launches of the Chebyshev step kernel since sq_setup, by variant, into counts[4] (host):
  *   counts[0]  projections of the block's atom images staged in shared memory, projector
  *              phases on tensor cores (SQ_MIXED, at most 4 channels per atom)
  *   counts[1]  staged in shared memory, scalar projector phases (SQ_FP64, or > 4 channels)
  *   counts[2]  projections read and accumulated in global memory (a block meets more
  *              projector rows than shared memory holds: dense atoms, large R_cut)
- * The environment variable SQ_STEP_SMEM_ROWS, read by sq_setup, lowers the row count above
- * which a block uses global memory (tuning and tests). Errors: SQ_ERR_INVALID_ARG. */
+ *   counts[3]  the TMA-staged step (SQ_MIXED, at most 4 channels per atom, one projector
+ *              radius per instance, selected by SQ_STEP_KERNEL=staged): every input of a brick
+ *              (t^j with its stencil halo, W, t^{j-1}, the projector values of the images meeting
+ *              it) copied into shared memory by the tensor memory accelerator
+ * The environment variables, read by sq_setup: SQ_STEP_SMEM_ROWS lowers the row count above
+ * which a block uses global memory (tuning and tests); SQ_STEP_KERNEL=staged puts a mixed handle
+ * on the TMA-staged step where its shared memory fits, SQ_STAGE_RECS (1..64, default 16) sets
+ * the atom images per stage. Errors: SQ_ERR_INVALID_ARG. */
 int sq_step_launch_counts(const sq_handle* h, long long* counts);
 
 /* Autotuning hook of the step kernel: n_warps warps per step block (1..8; 0 = the default,

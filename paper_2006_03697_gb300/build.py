@@ -18,7 +18,7 @@ SRC = PKG / "csrc"
 OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libsq_gb300.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sq_api.cu", "sq_setup.cu", "sq_sweep.cu", "sq_reduce.cu", "sq_lanczos.cu", "sq_noalloc.cu", "sq_batch.cu", "sq_serve.cu", "sq_gk.cu", "sq_gauss.cu"]
+SOURCES = ["sq_api.cu", "sq_setup.cu", "sq_sweep.cu", "sq_step_tma.cu", "sq_reduce.cu", "sq_lanczos.cu", "sq_noalloc.cu", "sq_batch.cu", "sq_serve.cu", "sq_gk.cu", "sq_gauss.cu"]
 
 
 def nvcc() -> str:

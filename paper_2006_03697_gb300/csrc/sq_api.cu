@@ -54,7 +54,10 @@ void place_atom(const sq::Geo& g, double rc, const double* pos, sq::AtomTab& at)
     at.R[a] = R;
     at.lo[a] = int(std::ceil((R - rc) / g.h[a]));
     const int hi = int(std::floor((R + rc) / g.h[a]));
-    at.dim[a] = std::min(std::max(0, hi - at.lo[a] + 1), box_extent_max(rc, g.h[a]));
+    // the box keeps the slot's full extent (the points past hi lie outside the sphere and hold
+    // zeros), so every table slot of a radius has one shape wherever the atom sits
+    (void)hi;
+    at.dim[a] = box_extent_max(rc, g.h[a]);
     at.dlo[a] = float(at.lo[a] * g.h[a] - R);
   }
 }
@@ -286,7 +289,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
   size_t tileB = size_t(g.B);
   P.per_tile_bytes = size_t(g.e_cap) * sizeof(sq::TileEntry) + 2 * sizeof(int) +
                      size_t(g.nbricks) * (size_t(g.br_cap) + 1) * sizeof(int) +
-                     size_t(g.nbricks) * size_t(g.br_cap) * 3 * sizeof(int4) +   // records + corner offsets
+                     size_t(g.nbricks) * size_t(g.br_cap) * 4 * sizeof(int4) +   // records, corner offsets, TMA boxes
                      3 * size_t(g.Upts) * tileB * real +        // T ring
                      3 * size_t(g.Upts) * tileB * real +        // W
                      2 * size_t(g.r_cap) * tileB * real +       // A, P
@@ -472,6 +475,14 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
     const long v = std::strtol(env, nullptr, 10);
     if (v >= 0 && v < h->step_rows_cap) h->step_rows_cap = int(v);
   }
+  // SQ_STEP_KERNEL=staged selects the TMA-staged step for a mixed sweep (sq_step_tma.cu; slower than
+  // the default step kernel on the workloads measured, kept for comparison), SQ_STAGE_RECS its
+  // images per stage
+  if (const char* env = std::getenv("SQ_STEP_KERNEL")) h->step_staged = std::string(env) == "staged";
+  if (const char* env = std::getenv("SQ_STAGE_RECS")) {
+    const long v = std::strtol(env, nullptr, 10);
+    if (v >= 1 && v <= 64) h->stage_recs_cap = int(v);
+  }
 
   auto cleanup = [&](int code) {
     g_setup_err = h->err;
@@ -515,6 +526,7 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->wb.brick_n, sizeof(int) * size_t(wt) * g.nbricks);
   SQ_ALLOC(h->wb.brick_rec, sizeof(int4) * 2 * size_t(wt) * g.nbricks * g.br_cap);
   SQ_ALLOC(h->wb.brick_d0, sizeof(float4) * size_t(wt) * g.nbricks * g.br_cap);
+  SQ_ALLOC(h->wb.brick_tma, sizeof(int4) * size_t(wt) * g.nbricks * g.br_cap);
   SQ_ALLOC(h->wb.slab_n, sizeof(int) * size_t(wt) * g.nslab);
   SQ_ALLOC(h->wb.slab_map, sizeof(int) * size_t(wt) * g.nslab * g.r_cap);
   for (int i = 0; i < 3; ++i) SQ_ALLOC(h->wb.T[i], real * size_t(wt) * g.Upts * g.B);
@@ -609,6 +621,8 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
     return cleanup(SQ_ERR_CUDA);
   }
   rc = sq::build_tables(h);
+  if (rc != SQ_OK) return cleanup(rc);
+  rc = sq::make_step_maps(h);
   if (rc != SQ_OK) return cleanup(rc);
   if (h->bounds_mode == SQ_BOUNDS_PER_NODE) {
     rc = sq::init_node_tables(h);
@@ -835,7 +849,7 @@ int sq_tune_step(sq_handle* h, int n_warps, int wave_tiles, int reps, double* ms
 
 int sq_step_launch_counts(const sq_handle* h, long long* counts) {
   if (!h || !counts) return SQ_ERR_INVALID_ARG;
-  for (int i = 0; i < 3; ++i) counts[i] = h->step_variant[i];
+  for (int i = 0; i < 4; ++i) counts[i] = h->step_variant[i];
   return SQ_OK;
 }
 

@@ -60,6 +60,7 @@ struct sq_batch {
   std::vector<sq_handle*> hs;
   int chains = 0;                       // parallel branches of the graph (members round-robin)
   std::vector<std::vector<int>> rows;   // wave layouts the graph was captured with
+  std::vector<std::vector<int>> recs;   // and the brick image counts (staged step)
   cudaStream_t s0 = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -138,7 +139,11 @@ int capture(sq_batch* b) {
     return SQ_ERR_CUDA;
   }
   b->rows.clear();
-  for (sq_handle* h : b->hs) b->rows.push_back(h->wave_rows);
+  b->recs.clear();
+  for (sq_handle* h : b->hs) {
+    b->rows.push_back(h->wave_rows);
+    b->recs.push_back(h->wave_recs);
+  }
   return SQ_OK;
 }
 
@@ -182,7 +187,9 @@ int sq_batch_run(sq_batch* b, double* mu_out, sq_energies* e_out, double* sigma_
   bool stale = !b->exec;
   for (int i = 0; i < n; ++i)
     for (size_t w = 0; w < b->hs[i]->wave_rows.size(); ++w)
-      if (b->rows[i].size() != b->hs[i]->wave_rows.size() || b->hs[i]->wave_rows[w] > b->rows[i][w]) stale = true;
+      if (b->rows[i].size() != b->hs[i]->wave_rows.size() || b->hs[i]->wave_rows[w] > b->rows[i][w] ||
+          b->recs[i].size() != b->hs[i]->wave_recs.size() || b->hs[i]->wave_recs[w] > b->recs[i][w])
+        stale = true;
   if (stale) {
     const int rc = capture(b);
     if (rc != SQ_OK) return rc;
@@ -205,6 +212,7 @@ int sq_batch_run(sq_batch* b, double* mu_out, sq_energies* e_out, double* sigma_
     int rc = SQ_OK;
     if (st[sq::kStBadBounds]) rc = sq::fail(h, SQ_ERR_CUDA, "spectral bounds are not finite or empty");
     else if (st[sq::kStOverflow]) rc = sq::fail(h, SQ_ERR_CUDA, "internal list capacity exceeded");
+    else if (st[sq::kStTimeout]) rc = sq::fail(h, SQ_ERR_TIMEOUT, "a staged step block's copy wait ran out");
     else if (st[sq::kStNoBracket]) rc = sq::fail(h, SQ_ERR_NO_BRACKET, "N(mu) - N_e has no sign change on the bisection bracket");
     h->bounds_ready = true;
     h->moments_ready = (rc == SQ_OK);

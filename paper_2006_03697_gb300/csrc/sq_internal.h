@@ -15,6 +15,7 @@
 //     4x4x4 brick of U the entries meeting the brick (used by the per-point nonlocal apply).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -104,6 +105,7 @@ struct WaveBufs {
   int* brick_n = nullptr;         // [wt][nbricks]
   int4* brick_rec = nullptr;      // [wt][nbricks][br_cap][2] per-brick image records
   float4* brick_d0 = nullptr;     // [wt][nbricks][br_cap] x - R of the record's brick corner (FP32 W table)
+  int4* brick_tma = nullptr;      // [wt][nbricks][br_cap] (atom, box-local x, y, z of the brick corner)
   int* slab_n = nullptr;          // [wt][nslab] projector rows meeting each slab (y-row of bricks)
   int* slab_map = nullptr;        // [wt][nslab][r_cap] slab row -> tile row
   void* T[3] = {nullptr, nullptr, nullptr};   // Real [wt][Upts][B]
@@ -178,6 +180,7 @@ struct sq_handle {
   bool proj4 = false;               // every atom has at most 4 projector channels (one group per image)
   std::vector<sq::Wave> waves;
   std::vector<int> wave_rows;       // per wave: most projector rows of a slab (shared-memory size)
+  std::vector<int> wave_recs;       // per wave: most atom images meeting one brick (staged step)
   int tile_begin = 0, tile_end = 0;   // tiles this handle sweeps (node partition)
   int wave_cap = 0;
   sq::Dev d;
@@ -185,8 +188,16 @@ struct sq_handle {
   std::vector<int> lanczos_tiles;
   long long launches = 0;
   // step-kernel launches by variant: [0] projections staged in shared memory, tensor-core
-  // projector phases; [1] shared memory, scalar phases; [2] projections in global memory
-  long long step_variant[3] = {0, 0, 0};
+  // projector phases; [1] shared memory, scalar phases; [2] projections in global memory;
+  // [3] the TMA-staged step (sq_step_tma.cu)
+  long long step_variant[4] = {0, 0, 0, 0};
+  // tensor maps of the TMA-staged step: t buffers (x, y, z sticks, brick), W, projector tables
+  CUtensorMap tmT[3][4];
+  CUtensorMap tmW;
+  CUtensorMap tmChi;
+  bool tma_ok = false;              // the maps exist and the instance fits the staged step
+  bool step_staged = false;         // SQ_STEP_KERNEL=staged: the TMA-staged step where it applies
+  int stage_recs_cap = 16;          // SQ_STAGE_RECS: atom images per stage of the staged step
   int step_rows_cap = 0;            // most projector rows a step block stages in shared memory
   int step_warps = 0;               // warps per step block (0: the brick-count rule; set by the tuner)
   // optional event timing of the sweep kernels
@@ -218,8 +229,16 @@ struct NvtxRange {
 int set_bounds(sq_handle* h, double lo, double hi);
 // The same scaling on the device from the Lanczos interval in scal[8], scal[9] (sq_lanczos.cu)
 int set_bounds_device(sq_handle* h);
-// per-wave slab row counts (sq_sweep.cu): sizes the step kernel's shared memory, once per layout
+// per-wave slab row counts and brick image counts (sq_sweep.cu): size the step kernels' shared
+// memory, once per layout
 int measure_wave_rows(sq_handle* h);
+// the TMA-staged FP32 step (sq_step_tma.cu): tensor maps (after the buffers exist), its shared
+// memory for a slab row count and a brick image count, and one launch on t buffers ic, ip
+constexpr size_t kStepTmaSmemMax = 220 * 1024;
+int make_step_maps(sq_handle* h);
+size_t step_tma_smem_bytes(int rows, int cap_rec);
+int launch_step_tma(sq_handle* h, const Wave& w, dim3 grid, int ic, int ip, float* Tn, const double* Pg, double* Pgn,
+                    int mode, int rows, int cap_rec);
 // one recurrence step launch (mode 1) of wave 0 with the handle's current settings, timed with
 // CUDA events on its stream (sq_sweep.cu; the autotuner's measurement)
 int time_step_launch(sq_handle* h, int reps, double* ms_out);

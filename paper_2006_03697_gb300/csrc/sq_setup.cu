@@ -134,8 +134,8 @@ __device__ __forceinline__ bool image_meets_box(const Geo& g, const TileEntry& t
 __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, const double* __restrict__ rcmax,
                               const TileEntry* __restrict__ entries, const int* __restrict__ n_entries,
                               int* __restrict__ blist, int* __restrict__ bn, int4* __restrict__ rec,
-                              float4* __restrict__ d0, int* __restrict__ slab_n, int* __restrict__ slab_map,
-                              int* __restrict__ status) {
+                              float4* __restrict__ d0, int4* __restrict__ tma, int* __restrict__ slab_n,
+                              int* __restrict__ slab_map, int* __restrict__ status) {
   const int br = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl), lane = threadIdx.x;
   int o[3];
   tile_origin(g, t, o);
@@ -220,6 +220,8 @@ __global__ void k_brick_lists(Geo g, Wave w, const AtomTab* __restrict__ atoms, 
         d0[((size_t)tl * g.nbricks + br) * g.br_cap + pos_s] =
             make_float4(float((ats.lo[0] + l0[0]) * g.h[0] - ats.R[0]), float((ats.lo[1] + l0[1]) * g.h[1] - ats.R[1]),
                         float((ats.lo[2] + l0[2]) * g.h[2] - ats.R[2]), 0.f);
+        // the brick's box in the atom's table slot (coordinates of the TMA-staged step)
+        tma[((size_t)tl * g.nbricks + br) * g.br_cap + pos_s] = make_int4(tes.atom, l0[0], l0[1], l0[2]);
       }
     }
     cnt += __popc(mask);
@@ -389,7 +391,7 @@ static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, const Real
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
                                                           h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.brick_d0,
-                                                          h->wb.slab_n, h->wb.slab_map, h->d.status);
+                                                          h->wb.brick_tma, h->wb.slab_n, h->wb.slab_map, h->d.status);
   SQ_LAUNCH_CHECK(h);
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
                                           (double*)h->wb.Pg[0], (double*)h->wb.Pg[1]);
@@ -410,7 +412,7 @@ int build_wave_entries(sq_handle* h, const Wave& w) {
   SQ_LAUNCH_CHECK(h);
   k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
                                                           h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.brick_d0,
-                                                          h->wb.slab_n, h->wb.slab_map, h->d.status);
+                                                          h->wb.brick_tma, h->wb.slab_n, h->wb.slab_map, h->d.status);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }

@@ -167,15 +167,7 @@ constexpr int kTileB = 8;   // nodes per tile (2 x 2 x 2); one warp = 4 points x
 // x = hi + lo with hi, lo TF32 (11 significant bits each); a product is taken as
 // hi*hi + hi*lo + lo*hi with FP32 accumulation (the lo*lo term, ~2^-22 relative, is dropped).
 
-// d (16 x 8, FP32) += a (16 x 8, TF32, row) * b (8 x 8, TF32, col); fragment of lane (g, t),
-// g = lane / 4, t = lane % 4: a = {(g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4)},
-// b = {(t, g), (t + 4, g)}, d = {(g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1)}
-__device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+// (mma_tf32: the warp-level m16n8k8 TF32 product, sq_device.cuh)
 
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
@@ -350,6 +342,7 @@ k_step(Geo g, Wave w, const Real* __restrict__ Tc, const Real* __restrict__ Tp, 
         split_tf32(p1, bh[1], bl[1]);
         const int dx = r1.x, plane = r1.x * r1.y * 4;
         // (hi, lo) pairs of channels ch, ch + 1 at point (pa0, pb0, 0): one 16-byte load per point
+        // (FP32 values split in the kernel instead halve these bytes but measured 3.5 % slower)
         const float* xb = chis + 2 * (r0.x + (pb0 * dx + pa0) * 4 + ch);
         const unsigned mlo = unsigned(r1.z) >> g8, mhi = unsigned(r1.w) >> g8;
 #pragma unroll
@@ -739,8 +732,8 @@ static int launch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, cons
       SQ_CUDA_TRY(h, cudaFuncSetAttribute(k_step<Real, NO, true, sizeof(Real) == 4>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmemMax));
       k_step<Real, NO, true, sizeof(Real) == 4><<<grid, nthr, smem, h->stream>>>(
-          h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.chi32s, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n,
-          v, h->d.scal, mode, h->wb.Spart, rows_smem, ncoef, h->d.status);
+          h->geo, w, Tc, Tp, Tn, Pg, Pgn, W, chi, h->d.chi32s, gdv, h->wb.brick_rec, h->wb.slab_n, h->wb.slab_map,
+          h->wb.brick_n, v, h->d.scal, mode, h->wb.Spart, rows_smem, ncoef, h->d.status);
       SQ_LAUNCH_CHECK(h);
       return SQ_OK;
     }
@@ -776,6 +769,22 @@ static int dispatch_step(sq_handle* h, const Wave& w, dim3 grid, size_t smem, co
   }
 }
 
+// images one stage of the TMA-staged step holds in wave wi: the wave's fullest brick, at most
+// kStepTmaRecs (a brick with more takes them in chunks)
+static int stage_recs(const sq_handle* h, size_t wi) {
+  return std::max(1, std::min(h->wave_recs[wi], h->stage_recs_cap));
+}
+
+// The TMA-staged step (sq_step_tma.cu), when selected (SQ_STEP_KERNEL=staged), runs a mixed sweep
+// wave when its maps exist and the slab's projections and one stage fit in shared memory.
+static bool use_tma(const sq_handle* h, size_t wi) {
+  if (!h->tma_ok || !h->step_staged || h->precision != SQ_MIXED) return false;
+  if (wi >= h->wave_rows.size() || wi >= h->wave_recs.size()) return false;
+  const int rows = std::max(1, h->wave_rows[wi]);
+  if (rows > h->step_rows_cap) return false;   // the global-memory projection path
+  return step_tma_smem_bytes(rows, stage_recs(h, wi)) <= kStepTmaSmemMax;
+}
+
 template <typename Real>
 static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv) {
   const Geo& g = h->geo;
@@ -787,7 +796,7 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SQ_CUDA_TRY(h, cudaStreamIsCapturing(s, &cap));
   const bool capturing = cap != cudaStreamCaptureStatusNone;
-  if (h->wave_rows.size() != h->waves.size()) {
+  if (h->wave_rows.size() != h->waves.size() || h->wave_recs.size() != h->waves.size()) {
     if (capturing) return fail(h, SQ_ERR_STATE, "wave layout not measured before capture");
     int rc = measure_wave_rows(h);
     if (rc != SQ_OK) return rc;
@@ -819,7 +828,11 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
       const int mode = (j == g.n_pl) ? 2 : (j == 0 ? 0 : 1);
       const double vecs = (mode == 0) ? 2.0 : (mode == 1) ? 3.0 : 1.0;   // reads t^j (t^{j-1}), writes t^{j+1}
       cudaEvent_t ev = capturing ? nullptr : timing_begin(h, SQ_K_STENCIL, vecs * col_bytes);
-      rc = dispatch_step<Real>(h, w, gstencil, smem, Tc, Tp, Tn, Pg[j % 2], Pg[(j + 1) % 2], W, chi, gdv, v, mode);
+      if (sizeof(Real) == 4 && use_tma(h, wi))
+        rc = launch_step_tma(h, w, gstencil, j % 3, (j + 2) % 3, (float*)Tn, Pg[j % 2], Pg[(j + 1) % 2], mode,
+                             std::max(1, rmax), stage_recs(h, wi));
+      else
+        rc = dispatch_step<Real>(h, w, gstencil, smem, Tc, Tp, Tn, Pg[j % 2], Pg[(j + 1) % 2], W, chi, gdv, v, mode);
       if (rc != SQ_OK) return rc;
       timing_end(h, ev);
       ev = capturing ? nullptr : timing_begin(h, SQ_K_MOMENTS, 0.0);
@@ -838,6 +851,7 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
   SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
   if (st[kStOverflow]) return fail(h, SQ_ERR_CUDA, "internal list capacity exceeded");
   if (st[kStBadBounds]) return fail(h, SQ_ERR_CUDA, "spectral bounds are not finite or empty");
+  if (st[kStTimeout]) return fail(h, SQ_ERR_TIMEOUT, "a staged step block's copy wait ran out");
   return SQ_OK;
 }
 
@@ -849,7 +863,7 @@ static int time_step_t(sq_handle* h, int reps, double* ms_out, const Real* chi, 
     *ms_out = 0.0;
     return SQ_OK;
   }
-  if (h->wave_rows.size() != h->waves.size()) {
+  if (h->wave_rows.size() != h->waves.size() || h->wave_recs.size() != h->waves.size()) {
     int rc = measure_wave_rows(h);
     if (rc != SQ_OK) return rc;
   }
@@ -860,15 +874,21 @@ static int time_step_t(sq_handle* h, int reps, double* ms_out, const Real* chi, 
   double* Pg[2] = {(double*)h->wb.Pg[0], (double*)h->wb.Pg[1]};
   const size_t smem = std::max<size_t>(1, size_t(h->wave_rows[0])) * kTileB * (sizeof(double) + sizeof(Real));
   const dim3 grid(g.nslab, w.ntiles);
+  const bool tma = sizeof(Real) == 4 && use_tma(h, 0);
+  const int rows = std::max(1, h->wave_rows[0]), recs = stage_recs(h, 0);
   // the first launch (mode 0) forms t^1 from t^0, so the timed launches read defined values
-  rc = dispatch_step<Real>(h, w, grid, smem, T[0], T[2], T[1], Pg[0], Pg[1], (Real*)h->wb.W, chi, gdv, v, 0);
+  if (tma)
+    rc = launch_step_tma(h, w, grid, 0, 2, (float*)T[1], Pg[0], Pg[1], 0, rows, recs);
+  else
+    rc = dispatch_step<Real>(h, w, grid, smem, T[0], T[2], T[1], Pg[0], Pg[1], (Real*)h->wb.W, chi, gdv, v, 0);
   if (rc != SQ_OK) return rc;
   cudaEvent_t e0, e1;
   SQ_CUDA_TRY(h, cudaEventCreate(&e0));
   SQ_CUDA_TRY(h, cudaEventCreate(&e1));
   cudaEventRecord(e0, s);
   for (int r = 0; r < reps && rc == SQ_OK; ++r)
-    rc = dispatch_step<Real>(h, w, grid, smem, T[1], T[0], T[2], Pg[1], Pg[0], (Real*)h->wb.W, chi, gdv, v, 1);
+    rc = tma ? launch_step_tma(h, w, grid, 1, 0, (float*)T[2], Pg[1], Pg[0], 1, rows, recs)
+             : dispatch_step<Real>(h, w, grid, smem, T[1], T[0], T[2], Pg[1], Pg[0], (Real*)h->wb.W, chi, gdv, v, 1);
   cudaEventRecord(e1, s);
   float ms = 0.f;
   const cudaError_t e = cudaEventSynchronize(e1);
@@ -889,16 +909,20 @@ int time_step_launch(sq_handle* h, int reps, double* ms_out) {
 int measure_wave_rows(sq_handle* h) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  std::vector<int> nrows;
+  std::vector<int> nrows, nrecs;
   h->wave_rows.assign(h->waves.size(), 0);
+  h->wave_recs.assign(h->waves.size(), 0);
   for (size_t wi = 0; wi < h->waves.size(); ++wi) {
     const Wave& w = h->waves[wi];
     int rc = build_wave_entries(h, w);
     if (rc != SQ_OK) return rc;
     nrows.resize(size_t(w.ntiles) * g.nslab);
+    nrecs.resize(size_t(w.ntiles) * g.nbricks);
     SQ_CUDA_TRY(h, cudaMemcpyAsync(nrows.data(), h->wb.slab_n, sizeof(int) * nrows.size(), cudaMemcpyDeviceToHost, s));
+    SQ_CUDA_TRY(h, cudaMemcpyAsync(nrecs.data(), h->wb.brick_n, sizeof(int) * nrecs.size(), cudaMemcpyDeviceToHost, s));
     SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
     h->wave_rows[wi] = nrows.empty() ? 0 : *std::max_element(nrows.begin(), nrows.end());
+    h->wave_recs[wi] = nrecs.empty() ? 0 : *std::max_element(nrecs.begin(), nrecs.end());
   }
   return SQ_OK;
 }

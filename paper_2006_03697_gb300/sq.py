@@ -369,8 +369,8 @@ def sq_kernel_launches(h) -> int:
 
 def sq_step_launch_counts(h):
     """Step-kernel launches by variant: (shared memory + tensor cores, shared memory + scalar,
-    global-memory projections)."""
-    c = (C.c_longlong * 3)()
+    global-memory projections, TMA-staged step)."""
+    c = (C.c_longlong * 4)()
     _check(lib().sq_step_launch_counts(h, c), h)
     return tuple(int(x) for x in c)
 
