@@ -238,7 +238,9 @@ int sq_step_launch_counts(const sq_handle* h, long long* counts);
  * per launch (0 = as many as the buffers sized at sq_setup hold; waves are spread evenly over the
  * handle's tiles). The settings stay with the handle. With reps > 0 and ms_per_tile non-NULL,
  * also times reps recurrence-step launches of the first wave with CUDA events on the handle's
- * stream and returns milliseconds per tile and step (needs the bounds: after sq_moments, or
+ * stream and returns milliseconds per tile and step; with more than one wave this includes the
+ * rebuild of the wave's lists and W table that every sweep then pays, spread over its n_pl + 1
+ * steps (one wave keeps them across evaluations) (needs the bounds: after sq_moments, or
  * SQ_BOUNDS_GIVEN; the sweep buffers are reused, the moments table is not touched).
  * Synchronises. Errors: SQ_ERR_INVALID_ARG, SQ_ERR_STATE, SQ_ERR_CUDA. */
 int sq_tune_step(sq_handle* h, int n_warps, int wave_tiles, int reps, double* ms_per_tile);

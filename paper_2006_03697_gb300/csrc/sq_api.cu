@@ -316,6 +316,11 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
     const size_t nst = size_t(P.lz_cap);
     P.fixed_bytes += sizeof(double) * (size_t(k + 2) * nst * g.Upts * g.B + nst * size_t(g.r_cap) * g.B +
                                        nst * g.B * size_t(5 * k + 8)) + sizeof(int) * nst;
+    // the sample tiles' own entry and brick lists
+    P.fixed_bytes += nst * (size_t(g.e_cap) * sizeof(sq::TileEntry) + 2 * sizeof(int) +
+                            size_t(g.nbricks) * (size_t(g.br_cap) + 1) * sizeof(int) +
+                            size_t(g.nbricks) * size_t(g.br_cap) * 4 * sizeof(int4) +
+                            size_t(g.nslab) * (size_t(g.r_cap) + 1) * sizeof(int));
   }
   // the node partition: part part_rank of part_count equal contiguous tile ranges
   P.tile_begin = 0;
@@ -325,9 +330,11 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
     P.tile_end = int((long long)g.n_tiles * (d->part_rank + 1) / d->part_count);
   }
   const long long ntl = std::max(1, P.tile_end - P.tile_begin);
-  // tiles per wave: keep the per-wave working set under 24 GiB (fewer, larger launches: less
-  // per-wave setup and a smaller tail), with the tiles spread evenly over the waves
+  // tiles per wave: one wave when the whole working set fits in 64 GiB (its lists and W table are
+  // then built once and kept across evaluations), else waves of at most 24 GiB (fewer, larger
+  // launches: less per-wave setup and a smaller tail), with the tiles spread evenly over the waves
   size_t budget = size_t(24) << 30;
+  if (size_t(ntl) * P.per_tile_bytes <= (size_t(64) << 30)) budget = size_t(ntl) * P.per_tile_bytes;
   long long wc = std::max<long long>(1, (long long)(budget / std::max<size_t>(P.per_tile_bytes, 1)));
   wc = std::min<long long>(std::min<long long>(wc, ntl), 32768);
   const long long nwaves = (ntl + wc - 1) / wc;
@@ -544,6 +551,17 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
     SQ_ALLOC(h->d.lzP, sizeof(double) * nst * size_t(g.r_cap) * g.B);
     SQ_ALLOC(h->d.lzC, sizeof(double) * nst * g.B * size_t(5 * k + 8));
     SQ_ALLOC(h->d.lz_tiles, sizeof(int) * nst);
+    // list buffers of the sample tiles (the sweep's wave lists stay untouched by the bounds)
+    SQ_ALLOC(h->lzb.entries, sizeof(sq::TileEntry) * nst * g.e_cap);
+    SQ_ALLOC(h->lzb.n_entries, sizeof(int) * nst);
+    SQ_ALLOC(h->lzb.n_rows, sizeof(int) * nst);
+    SQ_ALLOC(h->lzb.brick_list, sizeof(int) * nst * g.nbricks * g.br_cap);
+    SQ_ALLOC(h->lzb.brick_n, sizeof(int) * nst * g.nbricks);
+    SQ_ALLOC(h->lzb.brick_rec, sizeof(int4) * 2 * nst * g.nbricks * g.br_cap);
+    SQ_ALLOC(h->lzb.brick_d0, sizeof(float4) * nst * g.nbricks * g.br_cap);
+    SQ_ALLOC(h->lzb.brick_tma, sizeof(int4) * nst * g.nbricks * g.br_cap);
+    SQ_ALLOC(h->lzb.slab_n, sizeof(int) * nst * g.nslab);
+    SQ_ALLOC(h->lzb.slab_map, sizeof(int) * nst * g.nslab * g.r_cap);
   }
   if (h->bounds_mode == SQ_BOUNDS_PER_NODE) {
     const int k = h->lanczos_k;
@@ -675,6 +693,7 @@ int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff) {
     if (!std::isfinite(pos[i])) return sq::fail(h, SQ_ERR_INVALID_ARG, "non-finite atom position");
   // new base images and support boxes inside each atom's fixed table slot
   for (int J = 0; J < g.n_atoms; ++J) place_atom(g, h->rcmax_h[J], pos + 3 * J, h->atoms_h[J]);
+  h->atoms_epoch++;   // the kept wave lists and W table describe the old positions
   cudaStream_t s = h->stream;
   std::vector<float> v32(h->Nd);
   for (int i = 0; i < h->Nd; ++i) v32[i] = float(v_eff[i]);

@@ -239,7 +239,7 @@ static int gauss_t(sq_handle* h, int k, double* mu_out, double* rho_host, double
     rc = fail(h, SQ_ERR_CUDA, "status reset failed");
   for (int t0 = 0; t0 < g.n_tiles && rc == SQ_OK; t0 += wt) {
     const Wave w{t0, std::min(wt, g.n_tiles - t0), nullptr};
-    rc = lanczos_columns<Real>(h, w, 1, k, V, W, P, C);
+    rc = lanczos_columns<Real>(h, w, 1, k, V, W, P, C, &h->wb);
     if (rc != SQ_OK) break;
     const int ncols = w.ntiles * g.B;
     const double* alpha = C + (size_t)3 * ncols * (k + 1);

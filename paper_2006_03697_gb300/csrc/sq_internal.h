@@ -185,6 +185,16 @@ struct sq_handle {
   int wave_cap = 0;
   sq::Dev d;
   sq::WaveBufs wb;
+  sq::WaveBufs lzb;                 // list buffers of the Lanczos sample tiles (default bounds)
+  // what wb's lists (and W, A) describe: the wave, the atom positions (epoch, bumped by
+  // sq_update_atoms) and whether W was built too; a sweep of the same wave reuses them
+  struct ListsKey {
+    int tile0 = -1, ntiles = 0;
+    const int* ids = nullptr;
+    long long epoch = -1;
+    bool full = false;
+  } lists_key;
+  long long atoms_epoch = 0;
   std::vector<int> lanczos_tiles;
   long long launches = 0;
   // step-kernel launches by variant: [0] projections staged in shared memory, tensor-core
@@ -268,23 +278,27 @@ int timing_collect(sq_handle* h);
 // setup kernels (sq_setup.cu)
 int build_tables(sq_handle* h);
 int init_node_tables(sq_handle* h);   // per-node bounds mode: cosine table, neutral node bounds
-int build_wave_lists(sq_handle* h, const Wave& w);
+// the lists, A, W and t^0 of a wave in wb; with reuse, the lists and W of the same wave and atom
+// positions built by the previous sweep are kept (only A, the projection buffers and t^0 are
+// rewritten)
+int build_wave_lists(sq_handle* h, const Wave& w, bool reuse);
 
 // sweep (sq_sweep.cu)
 int run_sweep(sq_handle* h);
 int step_rows_smem_max(int precision);
 // out = H_q v for every node column of the wave's tiles (FP64), P = projection scratch
 // H_q v on the sample tiles of the Lanczos bounds (FP64 or FP32 vectors, matching tables)
-int launch_apply_h(sq_handle* h, const Wave& w, const double* v, double* out, double* P);
-int launch_apply_h(sq_handle* h, const Wave& w, const float* v, float* out, float* P);
-// entries / brick lists of a wave only (no A, W, t^0)
-int build_wave_entries(sq_handle* h, const Wave& w);
+int launch_apply_h(sq_handle* h, const Wave& w, const double* v, double* out, double* P, const WaveBufs& b);
+int launch_apply_h(sq_handle* h, const Wave& w, const float* v, float* out, float* P, const WaveBufs& b);
+// entries / brick lists of a wave only (no A, W, t^0), into b (the sweep's wb by default)
+int build_wave_entries(sq_handle* h, const Wave& w, WaveBufs* b = nullptr);
 
 // bounds / Fermi level / contraction (sq_reduce.cu)
 int run_lanczos(sq_handle* h);
 // k-step Lanczos of every node column of a wave (start 0: hash vector, 1: e_q); see sq_lanczos.cu
 template <typename Real>
-int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C);
+int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C,
+                    WaveBufs* b);
 int run_fermi(sq_handle* h, double* mu_out);
 // per-node bounds mode (sq_lanczos.cu, sq_reduce.cu)
 int run_lanczos_nodes(sq_handle* h);

@@ -305,7 +305,8 @@ __global__ void k_lz_node_bounds(Geo g, Wave w, int k, const double* __restrict_
 // k + 1 vectors of the wave, W one, P the projections; C is (5 k + 8) doubles per column:
 // cA, cB, nrm [ncols][k + 1], alpha, beta [ncols][k], keff (ints) - see lz_alpha etc.
 template <typename Real>
-int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C) {
+int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real* W, Real* P, double* C,
+                    WaveBufs* b) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
   const int nst = w.ntiles;
@@ -324,7 +325,7 @@ int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real
   const int eb = 1024;
   const int ub = int(std::min<size_t>(64, ((size_t)g.Upts * g.B + 255) / 256));   // update blocks per tile
   const int cb = (ncols + 127) / 128;
-  int rc = build_wave_entries(h, w);
+  int rc = build_wave_entries(h, w, b);
   if (rc != SQ_OK) return rc;
   if (start == 0) k_lz_init<Real><<<eb, 256, 0, s>>>(g, w, V);
   else k_lz_init_unit<Real><<<eb, 256, 0, s>>>(g, w, V);
@@ -337,7 +338,7 @@ int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real
   SQ_LAUNCH_CHECK(h);
   for (int i = 0; i < kk; ++i) {
     Real* Vi = V + (size_t)i * vstride;
-    rc = launch_apply_h(h, w, Vi, W, P);
+    rc = launch_apply_h(h, w, Vi, W, P, *b);
     if (rc != SQ_OK) return rc;
     k_lz_dots<Real><<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cA, ld);
     SQ_LAUNCH_CHECK(h);
@@ -359,8 +360,8 @@ int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real
   return SQ_OK;
 }
 
-template int lanczos_columns<float>(sq_handle*, const Wave&, int, int, float*, float*, float*, double*);
-template int lanczos_columns<double>(sq_handle*, const Wave&, int, int, double*, double*, double*, double*);
+template int lanczos_columns<float>(sq_handle*, const Wave&, int, int, float*, float*, float*, double*, WaveBufs*);
+template int lanczos_columns<double>(sq_handle*, const Wave&, int, int, double*, double*, double*, double*, WaveBufs*);
 
 template <typename Real>
 static int run_lanczos_t(sq_handle* h) {
@@ -368,8 +369,9 @@ static int run_lanczos_t(sq_handle* h) {
   const int k = h->lanczos_k;
   const int ncols = nst * h->geo.B;
   const Wave w{0, nst, h->d.lz_tiles};
+  // the sample tiles' lists go to their own buffers, so the sweep's lists (and W) stay valid
   int rc = lanczos_columns<Real>(h, w, 0, k, reinterpret_cast<Real*>(h->d.lzV), reinterpret_cast<Real*>(h->d.lzW),
-                                 reinterpret_cast<Real*>(h->d.lzP), h->d.lzC);
+                                 reinterpret_cast<Real*>(h->d.lzP), h->d.lzC, &h->lzb);
   if (rc != SQ_OK) return rc;
   const double* alpha = h->d.lzC + (size_t)3 * ncols * (k + 1);
   const double* beta = alpha + (size_t)ncols * k;
@@ -426,7 +428,7 @@ static int run_lanczos_nodes_t(sq_handle* h) {
   for (int t0 = h->tile_begin; t0 < h->tile_end; t0 += h->nlz_wave) {
     const Wave w{t0, std::min(h->nlz_wave, h->tile_end - t0), nullptr};
     int rc = lanczos_columns<Real>(h, w, 0, k, reinterpret_cast<Real*>(h->d.nV), reinterpret_cast<Real*>(h->d.nW),
-                                   reinterpret_cast<Real*>(h->d.nP), h->d.nC);
+                                   reinterpret_cast<Real*>(h->d.nP), h->d.nC, &h->wb);
     if (rc != SQ_OK) return rc;
     const int ncols = w.ntiles * g.B;
     const double* alpha = h->d.nC + (size_t)3 * ncols * (k + 1);

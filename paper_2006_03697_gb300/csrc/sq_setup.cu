@@ -383,36 +383,43 @@ __global__ void k_init_t0(Geo g, Wave w, Real* __restrict__ T0) {
 }
 
 template <typename Real>
-static int wave_lists_t(sq_handle* h, const Wave& w, const Real* chi, const Real* gdvR, Real* A, Real* W, Real* T0) {
+static int wave_lists_t(sq_handle* h, const Wave& w, bool reuse, const Real* chi, const Real* gdvR, Real* A, Real* W,
+                        Real* T0) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows,
-                                          h->d.status);
-  SQ_LAUNCH_CHECK(h);
-  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.brick_d0,
-                                                          h->wb.brick_tma, h->wb.slab_n, h->wb.slab_map, h->d.status);
-  SQ_LAUNCH_CHECK(h);
+  const sq_handle::ListsKey& key = h->lists_key;
+  const bool same = reuse && key.full && key.tile0 == w.tile0 && key.ntiles == w.ntiles && key.ids == w.ids &&
+                    key.epoch == h->atoms_epoch;
+  if (!same) {
+    int rc = build_wave_entries(h, w);
+    if (rc != SQ_OK) return rc;
+  }
   k_atable<Real><<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->d.gdv, chi, h->wb.entries, h->wb.n_entries, A,
                                           (double*)h->wb.Pg[0], (double*)h->wb.Pg[1]);
   SQ_LAUNCH_CHECK(h);
-  k_wtable<Real><<<dim3(g.nbr[2], w.ntiles), 224, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries, h->wb.brick_list,
-                                                          h->wb.brick_rec, h->wb.brick_d0, h->wb.brick_n, A, W);
-  SQ_LAUNCH_CHECK(h);
+  if (!same) {
+    k_wtable<Real><<<dim3(g.nbr[2], w.ntiles), 224, 0, s>>>(g, w, h->d.atoms, gdvR, chi, h->wb.entries,
+                                                            h->wb.brick_list, h->wb.brick_rec, h->wb.brick_d0,
+                                                            h->wb.brick_n, A, W);
+    SQ_LAUNCH_CHECK(h);
+    h->lists_key.full = true;
+  }
   SQ_CUDA_TRY(h, cudaMemsetAsync(T0, 0, sizeof(Real) * (size_t)w.ntiles * g.Upts * g.B, s));
   k_init_t0<Real><<<(w.ntiles + 31) / 32, dim3(g.B, 32), 0, s>>>(g, w, T0);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }
 
-int build_wave_entries(sq_handle* h, const Wave& w) {
+int build_wave_entries(sq_handle* h, const Wave& w, WaveBufs* b) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, h->wb.entries, h->wb.n_entries, h->wb.n_rows, h->d.status);
+  if (!b) b = &h->wb;
+  if (b == &h->wb) h->lists_key = {w.tile0, w.ntiles, w.ids, h->atoms_epoch, false};
+  k_tile_entries<<<w.ntiles, 256, 0, s>>>(g, w, h->d.atoms, b->entries, b->n_entries, b->n_rows, h->d.status);
   SQ_LAUNCH_CHECK(h);
-  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, h->wb.entries, h->wb.n_entries,
-                                                          h->wb.brick_list, h->wb.brick_n, h->wb.brick_rec, h->wb.brick_d0,
-                                                          h->wb.brick_tma, h->wb.slab_n, h->wb.slab_map, h->d.status);
+  k_brick_lists<<<dim3(g.nbricks, w.ntiles), 32, 0, s>>>(g, w, h->d.atoms, h->d.rcmax, b->entries, b->n_entries,
+                                                          b->brick_list, b->brick_n, b->brick_rec, b->brick_d0,
+                                                          b->brick_tma, b->slab_n, b->slab_map, h->d.status);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }
@@ -454,10 +461,12 @@ int init_node_tables(sq_handle* h) {
   return SQ_OK;
 }
 
-int build_wave_lists(sq_handle* h, const Wave& w) {
+int build_wave_lists(sq_handle* h, const Wave& w, bool reuse) {
   if (h->precision == SQ_FP64)
-    return wave_lists_t<double>(h, w, h->d.chi64, h->d.gdv64, (double*)h->wb.A, (double*)h->wb.W, (double*)h->wb.T[0]);
-  return wave_lists_t<float>(h, w, h->d.chi32, h->d.gdv32, (float*)h->wb.A, (float*)h->wb.W, (float*)h->wb.T[0]);
+    return wave_lists_t<double>(h, w, reuse, h->d.chi64, h->d.gdv64, (double*)h->wb.A, (double*)h->wb.W,
+                                (double*)h->wb.T[0]);
+  return wave_lists_t<float>(h, w, reuse, h->d.chi32, h->d.gdv32, (float*)h->wb.A, (float*)h->wb.W,
+                             (float*)h->wb.T[0]);
 }
 
 }  // namespace sq

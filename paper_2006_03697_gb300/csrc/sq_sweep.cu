@@ -804,7 +804,8 @@ static int sweep_t(sq_handle* h, const Real* chi, const Real* v, const Real* gdv
   for (size_t wi = 0; wi < h->waves.size(); ++wi) {
     NvtxRange nvtx("sweep wave");
     const Wave& w = h->waves[wi];
-    int rc = build_wave_lists(h, w);
+    // a captured graph must rebuild the lists itself (the atoms may move before it runs again)
+    int rc = build_wave_lists(h, w, !capturing);
     if (rc != SQ_OK) return rc;
     // largest slab projector-row count of the wave (measured once per layout) sizes the
     // per-slab shared accumulator
@@ -868,8 +869,23 @@ static int time_step_t(sq_handle* h, int reps, double* ms_out, const Real* chi, 
     if (rc != SQ_OK) return rc;
   }
   const Wave& w = h->waves[0];
-  int rc = build_wave_lists(h, w);
-  if (rc != SQ_OK) return rc;
+  cudaEvent_t e0, e1;
+  SQ_CUDA_TRY(h, cudaEventCreate(&e0));
+  SQ_CUDA_TRY(h, cudaEventCreate(&e1));
+  // with more than one wave every sweep rebuilds each wave's lists and W table: that cost, spread
+  // over the sweep's n_pl + 1 steps, belongs to the step time the tuner compares (one wave keeps
+  // them across evaluations)
+  const bool rebuilt = h->waves.size() > 1;
+  cudaEventRecord(e0, s);
+  int rc = build_wave_lists(h, w, !rebuilt);
+  cudaEventRecord(e1, s);
+  float ms_lists = 0.f;
+  if (rc == SQ_OK && rebuilt && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms_lists, e0, e1);
+  if (rc != SQ_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  }
   Real* T[3] = {(Real*)h->wb.T[0], (Real*)h->wb.T[1], (Real*)h->wb.T[2]};
   double* Pg[2] = {(double*)h->wb.Pg[0], (double*)h->wb.Pg[1]};
   const size_t smem = std::max<size_t>(1, size_t(h->wave_rows[0])) * kTileB * (sizeof(double) + sizeof(Real));
@@ -881,10 +897,11 @@ static int time_step_t(sq_handle* h, int reps, double* ms_out, const Real* chi, 
     rc = launch_step_tma(h, w, grid, 0, 2, (float*)T[1], Pg[0], Pg[1], 0, rows, recs);
   else
     rc = dispatch_step<Real>(h, w, grid, smem, T[0], T[2], T[1], Pg[0], Pg[1], (Real*)h->wb.W, chi, gdv, v, 0);
-  if (rc != SQ_OK) return rc;
-  cudaEvent_t e0, e1;
-  SQ_CUDA_TRY(h, cudaEventCreate(&e0));
-  SQ_CUDA_TRY(h, cudaEventCreate(&e1));
+  if (rc != SQ_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  }
   cudaEventRecord(e0, s);
   for (int r = 0; r < reps && rc == SQ_OK; ++r)
     rc = tma ? launch_step_tma(h, w, grid, 1, 0, (float*)T[2], Pg[1], Pg[0], 1, rows, recs)
@@ -897,7 +914,7 @@ static int time_step_t(sq_handle* h, int reps, double* ms_out, const Real* chi, 
   cudaEventDestroy(e1);
   if (rc != SQ_OK) return rc;
   if (e != cudaSuccess) return fail(h, SQ_ERR_CUDA, std::string("step timing: ") + cudaGetErrorString(e));
-  *ms_out = double(ms) / std::max(1, reps);
+  *ms_out = double(ms) / std::max(1, reps) + double(ms_lists) / (g.n_pl + 1);
   return SQ_OK;
 }
 
@@ -928,24 +945,25 @@ int measure_wave_rows(sq_handle* h) {
 }
 
 template <typename Real>
-static int apply_h_t(sq_handle* h, const Wave& w, const Real* v, Real* out, Real* P, const Real* chi, const Real* vpot) {
+static int apply_h_t(sq_handle* h, const Wave& w, const Real* v, Real* out, Real* P, const Real* chi, const Real* vpot,
+                     const WaveBufs& b) {
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
-  k_project<Real><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, chi, h->d.atoms, h->d.gdv, h->wb.entries,
-                                                               h->wb.n_entries, P);
+  k_project<Real><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, chi, h->d.atoms, h->d.gdv, b.entries,
+                                                               b.n_entries, P);
   SQ_LAUNCH_CHECK(h);
-  k_apply_h<Real><<<dim3(g.nbr[2], w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, chi, h->d.atoms, h->wb.entries,
-                                                               h->wb.brick_list, h->wb.brick_n, vpot);
+  k_apply_h<Real><<<dim3(g.nbr[2], w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, chi, h->d.atoms, b.entries,
+                                                               b.brick_list, b.brick_n, vpot);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
 }
 
-int launch_apply_h(sq_handle* h, const Wave& w, const double* v, double* out, double* P) {
-  return apply_h_t<double>(h, w, v, out, P, h->d.chi64, h->d.v64);
+int launch_apply_h(sq_handle* h, const Wave& w, const double* v, double* out, double* P, const WaveBufs& b) {
+  return apply_h_t<double>(h, w, v, out, P, h->d.chi64, h->d.v64, b);
 }
 
-int launch_apply_h(sq_handle* h, const Wave& w, const float* v, float* out, float* P) {
-  return apply_h_t<float>(h, w, v, out, P, h->d.chi32, h->d.v32);
+int launch_apply_h(sq_handle* h, const Wave& w, const float* v, float* out, float* P, const WaveBufs& b) {
+  return apply_h_t<float>(h, w, v, out, P, h->d.chi32, h->d.v32, b);
 }
 
 int run_sweep(sq_handle* h) {
