@@ -155,15 +155,16 @@ def step_kernel_hash() -> str:
     return hashlib.sha1((src[start:end] + dev).encode()).hexdigest()
 
 
-def stencil_traffic(sweep_hash: str):
-    """Per-launch DRAM traffic of the stencil kernel from the committed ncu summary, if it
+def stencil_traffic(sweep_hash: str, tiles_per_launch: float):
+    """Per-launch DRAM traffic of the stencil kernel: the committed ncu figure per tile (captured
+    on a smaller case of the same per-tile footprint) times the tiles of an average launch, if it
     was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "stencil_traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         if t.get("step_kernel_sha1") == sweep_hash:
-            return float(t["bytes_per_launch_full_size"])
+            return float(t["bytes_per_tile"]) * tiles_per_launch
     except (OSError, KeyError, ValueError):
         pass
     return None
@@ -556,8 +557,15 @@ def run_ours(args):
     st = kern["stencil"]
     sweep_hash = step_kernel_hash()
     achieved = (st["bytes"] / st["launches"]) / (st["ms"] / st["launches"] / 1000.0) / 1e9 if st["launches"] else 0.0
+    # tiles of an average step launch: this rank's tiles over the waves (n_pl + 1 launches per wave
+    # and evaluation)
+    tiles_part = int(np.prod((np.asarray(inst["n"], dtype=np.int64) + 1) // 2))
+    if part is not None:
+        tiles_part = tiles_part * (part[0] + 1) // part[1] - tiles_part * part[0] // part[1]
+    nwaves = max(1, round(st["launches"] / max(1, args.steps * (n_pl + 1))))
     roof = {"kernel": "k_stencil", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": stencil_traffic(sweep_hash),
+            "frac": achieved / hbm, "traffic": stencil_traffic(sweep_hash, tiles_part / nwaves),
+            "tiles_per_launch": tiles_part / nwaves,
             "peak_source": peak_kind, "dominant_kernel": dom,
             "algo_bytes_per_launch": st["bytes"] / max(1, st["launches"]),
             "avg_launch_ms": st["ms"] / max(1, st["launches"])}

@@ -195,6 +195,7 @@ struct sq_handle {
     bool full = false;
   } lists_key;
   long long atoms_epoch = 0;
+  long long lz_lists_epoch = -1;    // atom epoch of the Lanczos sample tiles' lists in lzb
   std::vector<int> lanczos_tiles;
   long long launches = 0;
   // step-kernel launches by variant: [0] projections staged in shared memory, tensor-core

@@ -325,8 +325,16 @@ int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real
   const int eb = 1024;
   const int ub = int(std::min<size_t>(64, ((size_t)g.Upts * g.B + 255) / 256));   // update blocks per tile
   const int cb = (ncols + 127) / 128;
-  int rc = build_wave_entries(h, w, b);
-  if (rc != SQ_OK) return rc;
+  // the sample tiles' lists (their own buffers) only change with the atoms; a graph capture
+  // records the build
+  int rc = SQ_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SQ_CUDA_TRY(h, cudaStreamIsCapturing(s, &cap));
+  if (b != &h->lzb || h->lz_lists_epoch != h->atoms_epoch || cap != cudaStreamCaptureStatusNone) {
+    rc = build_wave_entries(h, w, b);
+    if (rc != SQ_OK) return rc;
+    if (b == &h->lzb) h->lz_lists_epoch = h->atoms_epoch;
+  }
   if (start == 0) k_lz_init<Real><<<eb, 256, 0, s>>>(g, w, V);
   else k_lz_init_unit<Real><<<eb, 256, 0, s>>>(g, w, V);
   SQ_LAUNCH_CHECK(h);
