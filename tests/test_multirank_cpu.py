@@ -48,13 +48,14 @@ def test_single_process_passthrough():
 
 
 def test_stencil_traffic_figure_is_tied_to_the_profiled_kernel_text():
-    """bench.py reports the committed ncu DRAM traffic only for the step-kernel source it was
-    captured on (keyed by a hash of that text), else null."""
+    """bench.py reports the committed ncu DRAM traffic (per tile, times the tiles of a launch)
+    only for the step-kernel source it was captured on (keyed by a hash of that text), else
+    null; the committed figure is the current kernel's."""
     import json
     import os
     import bench
     path = os.path.join(os.path.dirname(os.path.abspath(bench.__file__)), "profiles", "stencil_traffic.json")
     t = json.load(open(path))
-    assert bench.stencil_traffic(t["step_kernel_sha1"]) == float(t["bytes_per_launch_full_size"])
-    assert bench.stencil_traffic("0" * 40) is None
-    assert len(bench.step_kernel_hash()) == 40
+    assert bench.stencil_traffic(t["step_kernel_sha1"], 8000) == float(t["bytes_per_tile"]) * 8000
+    assert bench.stencil_traffic("0" * 40, 8000) is None
+    assert bench.step_kernel_hash() == t["step_kernel_sha1"]
