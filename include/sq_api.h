@@ -159,6 +159,17 @@ int sq_fermi_level(sq_handle* h, double* mu_out);
  * Errors: SQ_ERR_INVALID_ARG (NULL or non-finite input), SQ_ERR_CUDA. */
 int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff);
 
+/* Fixed atoms across calls (e.g. SCF iterations of Sec. 5, where only V_eff changes): with
+ * enable != 0, the sweep keeps the per-tile atom-image lists, the brick records and the W_b
+ * table it built for the current atom positions across sq_moments calls (so do the Lanczos
+ * bounds for the lists of their sample tiles), instead of rebuilding them in every call. They
+ * depend on the positions only: sq_update_atoms with moved atoms discards them, with the same
+ * positions and a new V_eff it keeps them. Kept only when the handle's tiles form one wave
+ * (sq_footprint_bytes up to about 64 GiB of per-tile buffers). Off by default, where every
+ * sq_moments rebuilds them as a new snapshot needs. Results are identical either way.
+ * Errors: SQ_ERR_INVALID_ARG. */
+int sq_keep_lists(sq_handle* h, int enable);
+
 /* Node partition (part_count > 0): the moments of the nodes outside the handle's tile range
  * are zero, so R^j and every contraction output are this part's share of the node sums of
  * Sec. 4, and the parts add up to the whole cell. The Fermi level needs the whole-cell sums:

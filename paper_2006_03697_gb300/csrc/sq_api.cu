@@ -692,8 +692,13 @@ int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff) {
   for (int i = 0; i < 3 * g.n_atoms; ++i)
     if (!std::isfinite(pos[i])) return sq::fail(h, SQ_ERR_INVALID_ARG, "non-finite atom position");
   // new base images and support boxes inside each atom's fixed table slot
-  for (int J = 0; J < g.n_atoms; ++J) place_atom(g, h->rcmax_h[J], pos + 3 * J, h->atoms_h[J]);
-  h->atoms_epoch++;   // the kept wave lists and W table describe the old positions
+  bool moved = false;
+  for (int J = 0; J < g.n_atoms; ++J) {
+    const double R0[3] = {h->atoms_h[J].R[0], h->atoms_h[J].R[1], h->atoms_h[J].R[2]};
+    place_atom(g, h->rcmax_h[J], pos + 3 * J, h->atoms_h[J]);
+    for (int a = 0; a < 3; ++a) moved = moved || h->atoms_h[J].R[a] != R0[a];
+  }
+  if (moved) h->atoms_epoch++;   // kept wave lists and W table describe the old positions
   cudaStream_t s = h->stream;
   std::vector<float> v32(h->Nd);
   for (int i = 0; i < h->Nd; ++i) v32[i] = float(v_eff[i]);
@@ -706,14 +711,17 @@ int sq_update_atoms(sq_handle* h, const double* pos, const double* v_eff) {
     // the sample tiles follow argmin / argmax of the new V_eff
     std::vector<int> lz = lanczos_sample_tiles(g, v_eff);
     if (int(lz.size()) > h->lz_cap) return sq::fail(h, SQ_ERR_STATE, "Lanczos sample capacity exceeded");
+    if (lz != h->lanczos_tiles) h->lz_lists_epoch = -1;   // other sample tiles: their lists are rebuilt
     h->lanczos_tiles = lz;
     SQ_CUDA_TRY(h, cudaMemcpyAsync(h->d.lz_tiles, lz.data(), sizeof(int) * lz.size(), cudaMemcpyHostToDevice, s));
     h->bounds_ready = false;
   }
   int rc = sq::build_tables(h);
   if (rc != SQ_OK) return rc;
-  rc = sq::measure_wave_rows(h);   // the atoms moved: the slabs meet other projector rows
-  if (rc != SQ_OK) return rc;
+  if (moved) {
+    rc = sq::measure_wave_rows(h);   // the atoms moved: the slabs meet other projector rows
+    if (rc != SQ_OK) return rc;
+  }
   // pageable host sources: the copies have read them before the call returns; the handle's
   // results now describe the new snapshot only after the next sq_moments
   SQ_CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -863,6 +871,12 @@ int sq_tune_step(sq_handle* h, int n_warps, int wave_tiles, int reps, double* ms
     if (rc != SQ_OK) return rc;
     *ms_per_tile = h->waves.empty() ? 0.0 : ms / h->waves[0].ntiles;
   }
+  return SQ_OK;
+}
+
+int sq_keep_lists(sq_handle* h, int enable) {
+  if (!h) return SQ_ERR_INVALID_ARG;
+  h->keep_lists = enable != 0;
   return SQ_OK;
 }
 

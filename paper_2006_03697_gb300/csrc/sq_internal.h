@@ -195,6 +195,7 @@ struct sq_handle {
     bool full = false;
   } lists_key;
   long long atoms_epoch = 0;
+  bool keep_lists = false;          // sq_keep_lists: reuse the lists of unchanged atoms
   long long lz_lists_epoch = -1;    // atom epoch of the Lanczos sample tiles' lists in lzb
   std::vector<int> lanczos_tiles;
   long long launches = 0;

@@ -330,7 +330,7 @@ int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real
   int rc = SQ_OK;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SQ_CUDA_TRY(h, cudaStreamIsCapturing(s, &cap));
-  if (b != &h->lzb || h->lz_lists_epoch != h->atoms_epoch || cap != cudaStreamCaptureStatusNone) {
+  if (b != &h->lzb || !h->keep_lists || h->lz_lists_epoch != h->atoms_epoch || cap != cudaStreamCaptureStatusNone) {
     rc = build_wave_entries(h, w, b);
     if (rc != SQ_OK) return rc;
     if (b == &h->lzb) h->lz_lists_epoch = h->atoms_epoch;

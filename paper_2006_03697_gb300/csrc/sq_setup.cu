@@ -388,7 +388,7 @@ static int wave_lists_t(sq_handle* h, const Wave& w, bool reuse, const Real* chi
   const Geo& g = h->geo;
   cudaStream_t s = h->stream;
   const sq_handle::ListsKey& key = h->lists_key;
-  const bool same = reuse && key.full && key.tile0 == w.tile0 && key.ntiles == w.ntiles && key.ids == w.ids &&
+  const bool same = reuse && h->keep_lists && key.full && key.tile0 == w.tile0 && key.ntiles == w.ntiles && key.ids == w.ids &&
                     key.epoch == h->atoms_epoch;
   if (!same) {
     int rc = build_wave_entries(h, w);

@@ -872,10 +872,9 @@ static int time_step_t(sq_handle* h, int reps, double* ms_out, const Real* chi, 
   cudaEvent_t e0, e1;
   SQ_CUDA_TRY(h, cudaEventCreate(&e0));
   SQ_CUDA_TRY(h, cudaEventCreate(&e1));
-  // with more than one wave every sweep rebuilds each wave's lists and W table: that cost, spread
-  // over the sweep's n_pl + 1 steps, belongs to the step time the tuner compares (one wave keeps
-  // them across evaluations)
-  const bool rebuilt = h->waves.size() > 1;
+  // a sweep rebuilds each wave's lists and W table (unless sq_keep_lists holds them for one wave):
+  // that cost, spread over the sweep's n_pl + 1 steps, belongs to the step time the tuner compares
+  const bool rebuilt = h->waves.size() > 1 || !h->keep_lists;
   cudaEventRecord(e0, s);
   int rc = build_wave_lists(h, w, !rebuilt);
   cudaEventRecord(e1, s);

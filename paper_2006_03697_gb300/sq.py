@@ -31,7 +31,7 @@ EXPORTED = [
     "sq_setup", "sq_moments", "sq_fermi_level", "sq_node_sums", "sq_fermi_level_sums",
     "sq_density_energy_stress",
     "sq_density_energy_stress_dev", "sq_pressure", "sq_get_bounds", "sq_node_bounds", "sq_moments_copy", "sq_footprint_bytes",
-    "sq_kernel_launches", "sq_step_launch_counts", "sq_tune_step", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate",
+    "sq_kernel_launches", "sq_keep_lists", "sq_step_launch_counts", "sq_tune_step", "sq_kernel_timing", "sq_kernel_timing_read", "sq_fermi_level_noalloc", "sq_batch_evaluate",
     "sq_batch_create", "sq_batch_set_chains", "sq_batch_run", "sq_batch_last_error", "sq_batch_destroy", "sq_server_create", "sq_server_submit", "sq_server_submit_traj", "sq_server_resident",
     "sq_update_atoms",
     "sq_server_poll", "sq_server_pending", "sq_server_destroy", "sq_gauss_density", "sq_green_kubo", "sq_destroy",
@@ -107,6 +107,8 @@ def lib():
         L.sq_kernel_launches.restype = C.c_longlong
         L.sq_tune_step.argtypes = [H, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
         L.sq_tune_step.restype = C.c_int
+        L.sq_keep_lists.argtypes = [H, C.c_int]
+        L.sq_keep_lists.restype = C.c_int
         L.sq_step_launch_counts.argtypes = [H, C.POINTER(C.c_longlong)]
         L.sq_step_launch_counts.restype = C.c_int
         L.sq_kernel_timing.argtypes = [H, C.c_int]
@@ -365,6 +367,12 @@ def sq_footprint_bytes(desc: Desc) -> int:
 
 def sq_kernel_launches(h) -> int:
     return int(lib().sq_kernel_launches(h))
+
+
+def sq_keep_lists(h, enable: bool = True):
+    """Keeps the sweep's lists and W table of unchanged atom positions across sq_moments calls
+    (SCF iterations with fixed atoms); off by default."""
+    _check(lib().sq_keep_lists(h, 1 if enable else 0), h)
 
 
 def sq_step_launch_counts(h):

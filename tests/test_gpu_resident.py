@@ -130,3 +130,32 @@ def test_resident_handles_are_evicted_for_memory(sq):
     got = {r["tag"]: r for r in got}
     assert abs(got[0]["F"] - ra["F"]) <= 1e-10 * abs(ra["F"])
     assert abs(got[1]["F"] - rb["F"]) <= 1e-10 * abs(rb["F"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_keep_lists_for_fixed_atoms(sq, precision):
+    """SCF-like use (Sec. 5): the atoms stay, V_eff changes between evaluations. With
+    sq_keep_lists the sweep keeps the atom-image lists, brick records and W table of the
+    positions (and the Lanczos bounds the lists of their sample tiles): a repeated evaluation,
+    an evaluation after a new V_eff at the same positions, and one after the atoms move (which
+    discards them) must each equal a fresh setup of that snapshot (FP64 1e-10, mixed 1e-7)."""
+    mode = sq.SQ_FP64 if precision == "fp64" else sq.SQ_MIXED
+    base = _trajectory(n_snap=2, seed=11)
+    scf = dict(base[0])
+    scf["v_eff"] = 1.2 * np.asarray(base[0]["v_eff"]) - 0.05      # same atoms, new potential
+    nd = int(np.prod(base[0]["n"]))
+    rtol = 1e-10 if precision == "fp64" else 1e-7
+    h = sq.sq_setup(sq.Desc(base[0], mode, bounds=None))
+    try:
+        sq.sq_keep_lists(h, True)
+        first = _evaluate(sq, h, nd)
+        again = _evaluate(sq, h, nd)                                  # lists and W reused
+        ref0 = sq.run(base[0], mode, bounds=None)
+        _close(first, ref0, rtol)
+        _close(again, ref0, rtol)
+        sq.sq_update_atoms(h, scf["pos"], scf["v_eff"])
+        _close(_evaluate(sq, h, nd), sq.run(scf, mode, bounds=None), rtol)
+        sq.sq_update_atoms(h, base[1]["pos"], base[1]["v_eff"])      # moved: rebuilt
+        _close(_evaluate(sq, h, nd), sq.run(base[1], mode, bounds=None), rtol)
+    finally:
+        sq.sq_destroy(h)
