@@ -305,7 +305,7 @@ int make_plan(const sq_instance_desc* d, Plan& P, std::string& why) {
                   size_t(P.table_len) * (sizeof(double) + (real == sizeof(float) ? 3 * sizeof(float) : 0)) +
                   size_t(Nd) * size_t(d->n_pl + 1) * SQ_N_MOMENTS * sizeof(double) +   // moments
                   size_t(d->n_pl + 1) * 4 * sizeof(double) + size_t(M) * sizeof(double) +
-                  size_t(Nd) * sizeof(double) + 4096 * 32 * sizeof(double) + 1024;
+                  size_t(Nd) * sizeof(double) + 4096 * 32 * sizeof(double) + sq::kLzDotCap * sizeof(double) + 1024;
   // Lanczos sample tiles (argmin V, argmax V, a stride-n/2 node grid); the buffers hold the
   // largest count so that sq_update_atoms can move them with V
   P.lz_tiles.clear();
@@ -525,6 +525,7 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   SQ_ALLOC(h->d.part, sizeof(double) * 4096 * 32);
   SQ_ALLOC(h->d.rho, sizeof(double) * Nd);
   SQ_ALLOC(h->d.status, sizeof(int) * sq::kStCount);
+  SQ_ALLOC(h->d.lzdot, sizeof(double) * sq::kLzDotCap);
   const int wt = h->wave_cap;
   SQ_ALLOC(h->wb.entries, sizeof(sq::TileEntry) * size_t(wt) * g.e_cap);
   SQ_ALLOC(h->wb.n_entries, sizeof(int) * wt);

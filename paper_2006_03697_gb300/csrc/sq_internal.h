@@ -34,6 +34,7 @@ constexpr int kBrick = 4;        // brick side in points
 constexpr int kMaxCh = 8;        // projector channels per atom
 constexpr int kThreads = 256;    // block size of the tile kernels
 constexpr int kMaxU = 2 * 64 + 8; // largest union-window extent (m <= 64, b = 2, x padded to 4)
+constexpr size_t kLzDotCap = 8192;   // doubles of the Lanczos dot-product chunk partials
 
 struct AtomTab {
   int lo[3];        // support box corner (absolute lattice coordinates of the base image)
@@ -140,6 +141,7 @@ struct Dev {
   double* lzP = nullptr;          // projections of the Lanczos vector [nst][r_cap][B]
   double* lzC = nullptr;          // Gram-Schmidt coefficients / alpha, beta [cols][...]
   int* lz_tiles = nullptr;        // sample tile ids [nst]
+  double* lzdot = nullptr;        // chunk partials of the Lanczos dot products of small waves [kLzDotCap]
   // per-node bounds mode (SQ_BOUNDS_PER_NODE)
   double* nbnd = nullptr;         // [N_d][2] effective (lo, hi) of every node
   double* ncoef = nullptr;        // [N_d][2] step coefficients (ca = 2 / zeta_q, cd = ca lap0 - 2 chi_q / zeta_q)

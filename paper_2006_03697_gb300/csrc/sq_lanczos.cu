@@ -20,6 +20,7 @@ namespace sq {
 
 constexpr int kTileLz = 8;              // nodes per tile (columns per tile)
 constexpr int kMaxLanczosVecs = 136;    // Krylov vectors held (k + 1, k <= 128 + 7)
+constexpr int kLzDotChunks = 32;        // most chunks a dot product of a small wave is split into
 
 // Start vector of the column of node q: 1 + (hash(i, node) mod 1009) / 1009 on the window
 // (i = window-local index, C order z, y, x), zero elsewhere; normalised afterwards.
@@ -86,6 +87,64 @@ __global__ void k_lz_dots(Geo g, Wave w, const Real* __restrict__ V, int nvec, s
     for (int th = q; th < kThreads; th += g.B) t += red[th];
     out[((size_t)tl * g.B + q) * ld + i] = t;
   }
+}
+
+// The same products for waves of few tiles (the Lanczos sample tiles): block (i, tile, c) sums
+// chunk c of the tile's vector pair into part[((tile * nvec + i) * nch + c) * B + node], and
+// k_lz_dots_sum adds the nch chunks of every (tile, node, i) in order, so a product spreads over
+// nch times more blocks and the result does not depend on scheduling.
+template <typename Real>
+__global__ void k_lz_dots_part(Geo g, Wave w, const Real* __restrict__ V, int nvec, size_t vstride,
+                               const Real* __restrict__ x, double* __restrict__ part, int nch) {
+  const int i = blockIdx.x, tl = blockIdx.y, c = blockIdx.z;
+  const size_t n = (size_t)g.Upts * g.B;
+  const size_t len = ((n + nch - 1) / nch + g.B - 1) / g.B * g.B;   // chunks start at a node-0 slot
+  const size_t e0 = (size_t)c * len, e1 = min(n, e0 + len);
+  const size_t base = (size_t)tl * n;
+  const Real* Vi = V + (size_t)i * vstride + base;
+  const Real* xt = x + base;
+  const int q = threadIdx.x % g.B;
+  Real s = Real(0);
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) s += Vi[e] * xt[e];
+  __shared__ double red[kThreads];
+  red[threadIdx.x] = double(s);
+  __syncthreads();
+  if (threadIdx.x < g.B) {
+    double t = 0.0;
+    for (int th = q; th < kThreads; th += g.B) t += red[th];
+    part[(((size_t)tl * nvec + i) * nch + c) * g.B + q] = t;
+  }
+}
+
+__global__ void k_lz_dots_sum(const double* __restrict__ part, int ntiles, int nvec, int nch, int B,
+                              double* __restrict__ out, int ld) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ntiles * nvec * B) return;
+  const int q = k % B, i = (k / B) % nvec, tl = k / (B * nvec);
+  double t = 0.0;
+  for (int c = 0; c < nch; ++c) t += part[(((size_t)tl * nvec + i) * nch + c) * B + q];
+  out[((size_t)tl * B + q) * ld + i] = t;
+}
+
+// out[(tile node) * ld + i] = V_i . x per node column, one launch (or two for few tiles)
+template <typename Real>
+static int lz_dots(sq_handle* h, const Wave& w, const Real* V, int nvec, size_t vstride, const Real* x, double* out,
+                   int ld) {
+  const Geo& g = h->geo;
+  cudaStream_t s = h->stream;
+  const int blocks = nvec * w.ntiles;
+  const int nch = std::max(1, std::min(kLzDotChunks, (2 * 152 + blocks - 1) / std::max(1, blocks)));
+  if (blocks >= 2 * 152 || !h->d.lzdot || size_t(blocks) * nch * g.B > kLzDotCap) {
+    k_lz_dots<Real><<<dim3(nvec, w.ntiles), kThreads, 0, s>>>(g, w, V, nvec, vstride, x, out, ld);
+    SQ_LAUNCH_CHECK(h);
+    return SQ_OK;
+  }
+  k_lz_dots_part<Real><<<dim3(nvec, w.ntiles, nch), kThreads, 0, s>>>(g, w, V, nvec, vstride, x, h->d.lzdot, nch);
+  SQ_LAUNCH_CHECK(h);
+  const int nk = w.ntiles * nvec * g.B;
+  k_lz_dots_sum<<<(nk + 255) / 256, 256, 0, s>>>(h->d.lzdot, w.ntiles, nvec, nch, g.B, out, ld);
+  SQ_LAUNCH_CHECK(h);
+  return SQ_OK;
 }
 
 // x -= sum_i coef[col * ld + i] V_i; grid (blocks per tile, tiles): a block's coefficients
@@ -338,8 +397,8 @@ int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real
   if (start == 0) k_lz_init<Real><<<eb, 256, 0, s>>>(g, w, V);
   else k_lz_init_unit<Real><<<eb, 256, 0, s>>>(g, w, V);
   SQ_LAUNCH_CHECK(h);
-  k_lz_dots<Real><<<dim3(1, nst), kThreads, 0, s>>>(g, w, V, 1, vstride, V, nrm, ld);
-  SQ_LAUNCH_CHECK(h);
+  rc = lz_dots<Real>(h, w, V, 1, vstride, V, nrm, ld);
+  if (rc != SQ_OK) return rc;
   k_lz_mark_empty<<<cb, 128, 0, s>>>(ncols, nrm, ld, keff);
   SQ_LAUNCH_CHECK(h);
   k_lz_scale<Real><<<eb, 256, 0, s>>>(g, w, V, nrm, ld, keff, V, 1);
@@ -348,16 +407,16 @@ int lanczos_columns(sq_handle* h, const Wave& w, int start, int k, Real* V, Real
     Real* Vi = V + (size_t)i * vstride;
     rc = launch_apply_h(h, w, Vi, W, P, *b);
     if (rc != SQ_OK) return rc;
-    k_lz_dots<Real><<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cA, ld);
-    SQ_LAUNCH_CHECK(h);
+    rc = lz_dots<Real>(h, w, V, i + 1, vstride, W, cA, ld);
+    if (rc != SQ_OK) return rc;
     k_lz_update<Real><<<dim3(ub, nst), 256, 0, s>>>(g, w, V, i + 1, vstride, cA, ld, W);
     SQ_LAUNCH_CHECK(h);
-    k_lz_dots<Real><<<dim3(i + 1, nst), kThreads, 0, s>>>(g, w, V, i + 1, vstride, W, cB, ld);
-    SQ_LAUNCH_CHECK(h);
+    rc = lz_dots<Real>(h, w, V, i + 1, vstride, W, cB, ld);
+    if (rc != SQ_OK) return rc;
     k_lz_update<Real><<<dim3(ub, nst), 256, 0, s>>>(g, w, V, i + 1, vstride, cB, ld, W);
     SQ_LAUNCH_CHECK(h);
-    k_lz_dots<Real><<<dim3(1, nst), kThreads, 0, s>>>(g, w, W, 1, vstride, W, nrm, ld);
-    SQ_LAUNCH_CHECK(h);
+    rc = lz_dots<Real>(h, w, W, 1, vstride, W, nrm, ld);
+    if (rc != SQ_OK) return rc;
     k_lz_step<<<cb, 128, 0, s>>>(ncols, i, kk, k, cA, cB, ld, nrm, alpha, beta, keff);
     SQ_LAUNCH_CHECK(h);
     if (i < kk - 1) {

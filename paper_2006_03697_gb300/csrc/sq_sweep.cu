@@ -77,13 +77,15 @@ k_project(Geo g, Wave w, const Real* __restrict__ Tn, const Real* __restrict__ c
   }
 }
 
-// out = H_q v on every node window of the wave (zero outside the windows); P from k_project.
+// out = H_q v on every node window of the wave (zero outside the windows); P from k_project. One
+// block per (brick row: 4 y- and 4 z-planes of the window, all x; tile), so the few sample tiles
+// of the Lanczos bounds still spread over the GPU.
 template <typename Real>
 __global__ void __launch_bounds__(kThreads)
 k_apply_h(Geo g, Wave w, const Real* __restrict__ Tc, Real* __restrict__ Tn, const Real* __restrict__ P,
           const Real* __restrict__ chi, const AtomTab* __restrict__ atoms, const TileEntry* __restrict__ entries,
           const int* __restrict__ blist, const int* __restrict__ bn, const Real* __restrict__ v) {
-  const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
+  const int row = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
   int o[3];
   tile_origin(g, t, o);
   const int Ux = g.U[0], Uy = g.U[1], Uz = g.U[2], B = g.B;
@@ -91,15 +93,16 @@ k_apply_h(Geo g, Wave w, const Real* __restrict__ Tc, Real* __restrict__ Tn, con
   const Real* T = Tc + tbase;
   const Real* Pt = P + (size_t)tl * g.r_cap * B;
   const TileEntry* ent = entries + (size_t)tl * g.e_cap;
-  const int z0 = slab * kBrick, nz = min(kBrick, Uz - z0);
-  const int nel = Ux * Uy * nz * B;
+  const int z0 = (row / g.nbr[1]) * kBrick, nz = min(kBrick, Uz - z0);
+  const int y0 = (row % g.nbr[1]) * kBrick, ny = min(kBrick, Uy - y0);
+  const int nel = Ux * ny * nz * B;
   const int st[3] = {B, Ux * B, Ux * Uy * B};
   const int Ua[3] = {Ux, Uy, Uz};
   for (int i = threadIdx.x; i < nel; i += kThreads) {
     const int p = i / B, q = i % B;
     int qo[3];
     node_offset(g, q, qo);
-    const int ux = p % Ux, uy = (p / Ux) % Uy, uz = z0 + p / (Ux * Uy);
+    const int ux = p % Ux, uy = y0 + (p / Ux) % ny, uz = z0 + p / (Ux * ny);
     const size_t e = (size_t)((uz * Uy + uy) * Ux + ux) * B + q;
     if (!node_valid(g, o, qo) || !in_window(g, qo, ux, uy, uz)) {
       Tn[tbase + e] = Real(0);
@@ -951,7 +954,7 @@ static int apply_h_t(sq_handle* h, const Wave& w, const Real* v, Real* out, Real
   k_project<Real><<<dim3(g.e_cap, w.ntiles), kThreads, 0, s>>>(g, w, v, chi, h->d.atoms, h->d.gdv, b.entries,
                                                                b.n_entries, P);
   SQ_LAUNCH_CHECK(h);
-  k_apply_h<Real><<<dim3(g.nbr[2], w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, chi, h->d.atoms, b.entries,
+  k_apply_h<Real><<<dim3(g.nbr[2] * g.nbr[1], w.ntiles), kThreads, 0, s>>>(g, w, v, out, P, chi, h->d.atoms, b.entries,
                                                                b.brick_list, b.brick_n, vpot);
   SQ_LAUNCH_CHECK(h);
   return SQ_OK;
