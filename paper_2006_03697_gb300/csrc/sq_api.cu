@@ -486,6 +486,9 @@ int sq_setup(const sq_instance_desc* desc, sq_handle** out) {
   // the default step kernel on the workloads measured, kept for comparison), SQ_STAGE_RECS its
   // images per stage
   if (const char* env = std::getenv("SQ_STEP_KERNEL")) h->step_staged = std::string(env) == "staged";
+  // SQ_STAGE_WAIT_TEST=1: every stage of the staged step waits for 16 bytes that never come, so
+  // its bounded wait runs out (the test of SQ_ERR_TIMEOUT; the copies themselves complete)
+  if (const char* env = std::getenv("SQ_STAGE_WAIT_TEST")) h->stage_wait_test = std::string(env) == "1";
   if (const char* env = std::getenv("SQ_STAGE_RECS")) {
     const long v = std::strtol(env, nullptr, 10);
     if (v >= 1 && v <= 64) h->stage_recs_cap = int(v);

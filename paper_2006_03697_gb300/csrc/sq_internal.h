@@ -212,6 +212,7 @@ struct sq_handle {
   bool tma_ok = false;              // the maps exist and the instance fits the staged step
   bool step_staged = false;         // SQ_STEP_KERNEL=staged: the TMA-staged step where it applies
   int stage_recs_cap = 16;          // SQ_STAGE_RECS: atom images per stage of the staged step
+  bool stage_wait_test = false;     // SQ_STAGE_WAIT_TEST=1: the staged step's copy wait runs out (tests)
   int step_rows_cap = 0;            // most projector rows a step block stages in shared memory
   int step_warps = 0;               // warps per step block (0: the brick-count rule; set by the tuner)
   // optional event timing of the sweep kernels

@@ -273,7 +273,7 @@ __global__ void k_atable(Geo g, Wave w, const AtomTab* __restrict__ atoms, const
 // records: the 64-bit sphere mask skips the points an image does not reach, the table offset
 // of the brick corner locates the point's channel group.
 template <typename Real>
-__global__ void __launch_bounds__(224, sizeof(Real) == 4 ? 2 : 1) k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms,
+__global__ void __launch_bounds__(224, sizeof(Real) == 4 ? 4 : 1) k_wtable(Geo g, Wave w, const AtomTab* __restrict__ atoms,
                                                 const Real* __restrict__ gdv, const Real* __restrict__ chi,
                                                 const TileEntry* __restrict__ entries, const int* __restrict__ blist,
                                                 const int4* __restrict__ brec, const float4* __restrict__ bd0,

@@ -115,7 +115,8 @@ k_step_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUten
            const float* __restrict__ gdv, const int4* __restrict__ brec, const int4* __restrict__ btma,
            const int* __restrict__ slab_n, const int* __restrict__ slab_map, const int* __restrict__ bn,
            const float* __restrict__ v, const double* __restrict__ scal, int mode, double* __restrict__ Spart,
-           int rows_smem, int cap_rec, const double* __restrict__ ncoef, int* __restrict__ status) {
+           int rows_smem, int cap_rec, const double* __restrict__ ncoef, int* __restrict__ status,
+           int extra_tx) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int wrx[kMaxU], wry[kBrick], wrz[kMaxU];
   float* s_chi = reinterpret_cast<float*>(smem_raw);                 // [cap_rec][64 points][8]
@@ -135,6 +136,8 @@ k_step_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUten
   const int slab = blockIdx.x, tl = blockIdx.y, t = wave_tile(w, tl);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nsr = slab_n[(size_t)tl * g.nslab + slab];
+  // a copy wait of this sweep already ran out: its results are void, skip the work
+  if (*reinterpret_cast<volatile int*>(status + kStTimeout)) return;
   if (nsr > rows_smem) {   // a launch sized for another layout (e.g. a stale graph): refuse
     if (threadIdx.x == 0) atomicOr(status + kStOverflow, 4);
     return;
@@ -230,8 +233,9 @@ k_step_tma(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUten
   auto issue = [&](size_t bidx, int x0, int y0, int z0, int k0, int nc, bool core) {
     if (warp == 0) {
       if (lane == 0) {
+        // extra_tx > 0 (a test of the bounded wait) arms the phase for bytes that never arrive
         const uint32_t bytes = uint32_t((core ? 3 * kStickFloats * 4 + 3 * kCoreFloats * 4 : 0) +
-                                        (core && mode == 1 ? kCoreFloats * 4 : 0) + nc * kRecFloats * 4);
+                                        (core && mode == 1 ? kCoreFloats * 4 : 0) + nc * kRecFloats * 4 + extra_tx);
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, bytes);
       }
@@ -550,7 +554,7 @@ static void launch_tma(sq_handle* h, const Wave& w, dim3 grid, size_t smem, int 
   k_step_tma<NO><<<grid, kTmaThreads, smem, h->stream>>>(
       h->tmT[ic][0], h->tmT[ic][1], h->tmT[ic][2], h->tmT[ip][3], h->tmW, h->tmChi, h->geo, w, Tn, Pg, Pgn,
       h->d.gdv32, h->wb.brick_rec, h->wb.brick_tma, h->wb.slab_n, h->wb.slab_map, h->wb.brick_n, h->d.v32,
-      h->d.scal, mode, h->wb.Spart, rows, cap_rec, ncoef, h->d.status);
+      h->d.scal, mode, h->wb.Spart, rows, cap_rec, ncoef, h->d.status, h->stage_wait_test ? 16 : 0);
 }
 
 // Launches the staged step on buffers T[ic] (t^j), T[ip] (t^{j-1}) -> Tn; rows / cap_rec size the

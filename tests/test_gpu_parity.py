@@ -131,6 +131,36 @@ def test_staged_mixed_step(sq, monkeypatch, name):
         assert np.abs(g["moments"][:, :, k] - d["moments"][:, :, k]).max() <= 1e-4 * scale, k
 
 
+def test_staged_step_copy_wait_runs_out(sq, monkeypatch):
+    """The staged step's one device wait (its mbarrier phase of a brick's copies) is bounded:
+    with SQ_STAGE_WAIT_TEST=1 every stage is armed for 16 bytes more than its copies bring, so
+    the wait gives up after about 2e9 clock cycles, the block waits (bounded) for its copies and
+    leaves, the later launches of the sweep skip their work, and sq_moments returns
+    SQ_ERR_TIMEOUT within seconds. The context stays usable: a fresh handle then evaluates the
+    same instance to the oracle's bars."""
+    import time
+    inst = tiny_instance(**TINY["m1_no1"])
+    bounds = orc.lanczos_bounds(orc.Problem(inst))
+    monkeypatch.setenv("SQ_STEP_KERNEL", "staged")
+    monkeypatch.setenv("SQ_STAGE_WAIT_TEST", "1")
+    h = sq.sq_setup(sq.Desc(inst, sq.SQ_MIXED, bounds=bounds))
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(sq.SQError) as ei:
+            sq.sq_moments(h)
+        assert ei.value.code == sq.SQ_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 60.0
+        assert sq.sq_step_launch_counts(h)[3] > 0
+    finally:
+        sq.sq_destroy(h)
+    monkeypatch.delenv("SQ_STAGE_WAIT_TEST")
+    o = orc.run(inst, bounds=bounds)
+    g = sq.run(inst, sq.SQ_MIXED, bounds=bounds)
+    assert g["step_variants"][3] > 0
+    assert abs(g["F"] - o["F"]) <= E_RTOL_MIXED * max(1.0, abs(o["F"]))
+    assert np.abs(g["sigma"] - o["sigma"]).max() <= SIG_ATOL_MIXED
+
+
 # Hot dense hydrogen at the paper's density (2 g/cm^3 = 0.177 atoms / bohr^3, Sec. 5.2): 4 H in
 # a 2.7 x 2.7 x 3.15 bohr cell, s + p projectors.
 PAPER_DENSITY = dict(seed=7, n=(6, 6, 7), h=(0.45, 0.45, 0.45), n_atoms=4, n_o=3, r_cut=1.8, n_pl=12)
