@@ -35,7 +35,8 @@
  *     kernel or on the host. The one device wait is the TMA-staged step's wait for its own
  *     copies into shared memory (SQ_MIXED with SQ_STEP_KERNEL=staged): it gives up after about
  *     2e9 clock cycles (about a second), and the sweep then returns SQ_ERR_TIMEOUT (sq_moments,
- *     sq_batch_run).
+ *     sq_batch_run). The environment variable SQ_STAGE_WAIT_TEST=1, read by sq_setup, makes that
+ *     wait run out on purpose (for tests; the copies still complete).
  *   - The caller owns every host buffer passed in or out; the library copies inputs during
  *     sq_setup and owns all device memory of a handle until sq_destroy.
  *   - A handle is used by one host thread at a time. Work is issued on desc->stream
